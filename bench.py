@@ -1,0 +1,366 @@
+"""Benchmark of the fused expression + reduction path.
+
+Default workload (one step = one pass of the whole hot path over one batch):
+FP32 column-major 8192 x 8192 matrices A, B, C ~ U[-1, 1], D ~ U[0, 2]
+(seeded), and the calls a user makes for
+
+    out   = (A % B + 2 C) / (1 + abs(D))      with accu, norm2, min, max
+                                               of out in the same pass
+    chain = exp(-abs(A % B + 2 C)) / sqrt(1 + abs(D))
+    sum(out, 0), sum(out, 1)
+
+i.e. coot_expr_reduce (5 matrix streams), coot_expr_eval (5), and two
+coot_sum_dim over the stored out (1 each): 12 matrix streams of 268 MB =
+3.22 GB of algorithmic traffic per step.  `value` is that traffic over the
+device time of the step (GB/s); the inputs (1.07 GB) are larger than L2, so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl coot|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm: a deliberately slow
+program; parity and the roofline fraction are the headline).
+Under torchrun every rank runs its own instance (weak scaling, no
+collective); rank 0 prints the one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+N = 8192
+ELEM = 4
+MAT_BYTES = N * N * ELEM
+STREAMS = {"expr_reduce": 5, "expr_eval": 5, "sum_dim0": 1, "sum_dim1": 1}
+STEP_BYTES = sum(STREAMS.values()) * MAT_BYTES
+METRIC = "fused expr+reduction HBM GB/s (% of GB300 peak) vs unfused same GPU; batch evals/s"
+WORKLOAD = "matrices 8192x8192 fp32: (A%B+2C)/(1+|D|) with accu/norm2/min/max, exp/sqrt chain, sum dim 0 and 1"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def inputs_host(seed):
+    A = synth.uniform_f32(seed + 0, N * N)
+    B = synth.uniform_f32(seed + 1, N * N)
+    C = synth.uniform_f32(seed + 2, N * N)
+    D = synth.uniform_f32(seed + 3, N * N, 0.0, 2.0)
+    return [A, B, C, D]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the
+    timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle (CPU) legs
+
+def oracle_sample(seed, cols, time_budget=None):
+    """Run the oracle over the first `cols` columns of the workload; returns
+    (seconds, algorithmic bytes of the sample)."""
+    from oracle import coot_oracle as O
+    A = [synth.as_mat(synth.uniform_f32(seed + k, N * cols, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
+                      "f32", N, cols) for k in range(4)]
+    t_expr = O.encode(synth.MAT_EXPR)
+    t_chain = O.encode(synth.MAT_CHAIN)
+    t0 = time.perf_counter()
+    out = O.evaluate(t_expr, A)
+    O.accu(t_expr, A)
+    O.norm(t_expr, A, "fro")
+    O.minmax(t_expr, A)
+    O.evaluate(t_chain, A)
+    om = synth.as_mat(out.astype(np.float32).ravel(order="F"), "f32", N, cols)
+    leaf = O.encode(synth.LEAF0)
+    O.sum_dim(leaf, [om], 0)
+    O.sum_dim(leaf, [om], 1)
+    dt = time.perf_counter() - t0
+    return dt, sum(STREAMS.values()) * N * cols * ELEM
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cols = args.ref_cols
+    seed = synth.BASE_SEED + 1
+    oracle_sample(seed, 8)  # warm caches / imports
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(seed, cols)
+    for _ in range(args.steps):
+        dt, nbytes = oracle_sample(seed, cols)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    gbs = nbytes / (statistics.mean(times) * 1e9)
+    line = {"metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (oracle sample: first {cols} of 8192 columns)",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"8192 x {cols} column block of every matrix, whole step"},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def run_coot(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    coot.coot_init(local)
+    stream = torch.cuda.current_stream()
+    seed = synth.BASE_SEED + 1 + 1000 * rank
+    host = inputs_host(seed)
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    mats = [coot.Mat(t, N, N, N) for t in dev]
+    out1 = torch.empty(N * N, dtype=torch.float32, device="cuda")
+    out2 = torch.empty(N * N, dtype=torch.float32, device="cuda")
+    col = torch.empty(N, dtype=torch.float32, device="cuda")
+    row = torch.empty(N, dtype=torch.float32, device="cuda")
+    res = torch.empty(4, dtype=torch.float64, device="cuda")
+    ws = coot.Workspace(N)
+    t_expr = coot.serialize(synth.MAT_EXPR)
+    t_chain = coot.serialize(synth.MAT_CHAIN)
+    leaf = coot.serialize(synth.LEAF0)
+    heads = coot.HEAD_SUM | coot.HEAD_NORM2 | coot.HEAD_MIN | coot.HEAD_MAX
+    O1 = coot.Mat(out1, N, N, N)
+    O2 = coot.Mat(out2, N, N, N)
+    COL = coot.Mat(col, 1, N, 1)
+    ROW = coot.Mat(row, N, 1, N)
+    names = list(STREAMS)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        coot.coot_expr_reduce(t_expr, mats, heads, out=O1, out_dev=res, ws=ws)
+        if ev is not None:
+            ev[1].record(stream)
+        coot.coot_expr_eval(t_chain, mats, O2, ws=ws)
+        if ev is not None:
+            ev[2].record(stream)
+        coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws)
+        if ev is not None:
+            ev[3].record(stream)
+        coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)
+        if ev is not None:
+            ev[4].record(stream)
+
+    launches_per_step = 4
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    per_call = {n: [] for n in names}
+    for k in range(args.steps):
+        for i, n in enumerate(names):
+            per_call[n].append(evs[k][i].elapsed_time(evs[k][i + 1]))
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * STEP_BYTES / (ms_step * 1e-3) / 1e9
+
+    # unfused baseline of the same step: one kernel per node, temporaries in HBM
+    tmp = torch.empty(8 * N * N * 4, dtype=torch.uint8, device="cuda")
+
+    def step_unfused():
+        coot.coot_unfused_eval(t_expr, mats, O1, tmp=tmp)
+        coot.coot_accu(leaf, [O1], out_dev=res[0:1], ws=ws)
+        coot.coot_norm(leaf, [O1], "fro", out_dev=res[1:2], ws=ws)
+        coot.coot_minmax(leaf, [O1], out_dev=res[2:4], ws=ws)
+        coot.coot_unfused_eval(t_chain, mats, O2, tmp=tmp)
+        coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws)
+        coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)
+
+    for _ in range(3):
+        step_unfused()
+    torch.cuda.synchronize()
+    u0 = torch.cuda.Event(enable_timing=True)
+    u1 = torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    for _ in range(args.steps):
+        step_unfused()
+    u1.record(stream)
+    torch.cuda.synchronize()
+    ms_unfused = u0.elapsed_time(u1) / args.steps
+
+    # end to end through the API from pinned host buffers: inputs in, both
+    # stored results and every reduction out, every step
+    pinned_in = [torch.from_numpy(h).pin_memory() for h in host]
+    pin_out1 = torch.empty(N * N, dtype=torch.float32).pin_memory()
+    pin_out2 = torch.empty(N * N, dtype=torch.float32).pin_memory()
+    pin_col = torch.empty(N, dtype=torch.float32).pin_memory()
+    pin_row = torch.empty(N, dtype=torch.float32).pin_memory()
+    pin_res = torch.empty(4, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        for d, h in zip(dev, pinned_in):
+            d.copy_(h, non_blocking=True)
+        step()
+        pin_out1.copy_(out1, non_blocking=True)
+        pin_out2.copy_(out2, non_blocking=True)
+        pin_col.copy_(col, non_blocking=True)
+        pin_row.copy_(row, non_blocking=True)
+        pin_res.copy_(res, non_blocking=True)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e_steps = max(2, min(args.steps, 5))
+    barrier()
+    e0.record(stream)
+    for _ in range(e_steps):
+        step_e2e()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / e_steps
+    h2d = 4 * MAT_BYTES
+    d2h = 2 * MAT_BYTES + 2 * N * 4 + 4 * 8
+
+    peak, peak_kind = peaks()
+    dom = max(names, key=lambda n: statistics.mean(per_call[n]))
+    dom_ms = statistics.mean(per_call[dom])
+    achieved = STREAMS[dom] * MAT_BYTES / (dom_ms * 1e-3) / 1e9
+    calls = {n: {"ms": round(statistics.mean(per_call[n]), 4),
+                 "gbs": round(STREAMS[n] * MAT_BYTES / (statistics.mean(per_call[n]) * 1e-3) / 1e9, 1)}
+             for n in names}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, nbytes = oracle_sample(seed, args.cpu_cols)
+        cpu = {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"8192 x {args.cpu_cols} column block of every matrix, whole step, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_rows": N, "n_cols": N, "step_bytes": STEP_BYTES,
+                       "l2": "inputs larger than L2 (1.07 GB of inputs per step), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "frac_of_hbm_peak": round(value / world / peak, 4),
+            "unfused": {"ms_per_step": round(ms_unfused, 4),
+                        "value": round(world * STEP_BYTES / (ms_unfused * 1e-3) / 1e9, 1),
+                        "fused_speedup": round(ms_unfused / ms_step, 3)},
+            "calls": calls,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * STEP_BYTES / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+                    "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="coot", choices=["coot", "reference"])
+    ap.add_argument("--ref-cols", type=int, default=256, help="columns in each reference-arm step's sample")
+    ap.add_argument("--cpu-cols", type=int, default=1024, help="columns in the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_coot(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,290 @@
+/*
+ * coot.h - C ABI of the fused expression + reduction engine for GB300
+ * (sm_103a).
+ *
+ * The engine evaluates element-wise expression trees over column-major
+ * matrices and vectors in ONE fused GPU kernel per call, without
+ * temporaries, and can feed the element values straight into reductions.
+ * It implements the evaluation model of Bandicoot (Curtin, Edel, Sanderson,
+ * arXiv 2308.03120):
+ *   - expressions are trees of element-wise nodes (the paper's eOp / eGlue
+ *     expression types, Section 7) built from the operators of Table 2 and
+ *     the element-wise functions of Table 7;
+ *   - evaluation is delayed until the result is assigned (Section 7,
+ *     "operator="): the caller hands the whole tree over in one call;
+ *   - the reductions are those of Table 5 (accu, dot, norm) and Table 6
+ *     (sum / min / max along a dimension);
+ *   - matrices are column-major ("(i)" walks column by column, Table 1).
+ * Where the paper evaluates each tree node with at least one kernel launch
+ * (Section 7: it cannot generate code per expression), this library
+ * generates and compiles one kernel per tree at run time (cached).
+ *
+ * Memory and ownership.  Every pointer in a coot_mat, every result pointer
+ * (`out_dev`), every workspace (`ws`) and every stream belongs to the
+ * caller; the library never allocates or frees them.  Matrix and result
+ * pointers are DEVICE pointers unless a function says otherwise.  The
+ * library owns only its compiled-kernel cache.
+ *
+ * Asynchrony.  Calls enqueue work on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and return without waiting.  Results are valid
+ * once the stream has reached the call (cudaStreamSynchronize or an event).
+ * Host-side checks happen before anything is enqueued: on any error status
+ * nothing has been enqueued and no output has been written.
+ *
+ * Errors.  Every function returns a coot_status; nothing throws across the
+ * ABI.  coot_last_error() returns a message for the most recent failing
+ * call on the calling thread.  A CUDA error raised by a launch is returned
+ * as COOT_ERR_CUDA.
+ *
+ * Workspace.  Reductions need a small scratch area (`ws`, `ws_bytes`) for
+ * per-block partial results and arrival counters.  coot_workspace_size()
+ * gives a size that suffices for every call on operands of up to a given
+ * row count; a call checks `ws_bytes` and picks a launch shape that fits,
+ * or returns COOT_ERR_WORKSPACE.  The caller allocates the workspace on the
+ * device and ZERO-FILLS it once before its first use.  Every call that
+ * completes leaves the counters at zero again, so the same workspace can be
+ * reused by later calls on the same stream.  Two calls that run
+ * concurrently (different streams) need different workspaces.
+ *
+ * Aliasing.  An element-wise output may be exactly one of the inputs (same
+ * pointer, shape, dtype and ld): every element is read before it is written
+ * by the same thread, so "B = B + 3 * A" (the paper's Task 2, B += 3 * A) is
+ * valid.  Any other overlap between the output and an input is rejected
+ * with COOT_ERR_ALIAS.
+ */
+#ifndef COOT_H
+#define COOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum coot_status {
+  COOT_OK = 0,
+  COOT_ERR_INVALID_ARG = 1, /* null pointer, bad enum value, negative size   */
+  COOT_ERR_BAD_TREE = 2,    /* malformed serialised tree                      */
+  COOT_ERR_SHAPE = 3,       /* operand / output shapes do not conform         */
+  COOT_ERR_DTYPE = 4,       /* unsupported storage type for this operand      */
+  COOT_ERR_ALIAS = 5,       /* output partially overlaps an input             */
+  COOT_ERR_EMPTY = 6,       /* min/max of an object with no elements          */
+  COOT_ERR_UNSUPPORTED = 7, /* valid request this library does not implement  */
+  COOT_ERR_COMPILE = 8,     /* run-time compilation of a kernel failed        */
+  COOT_ERR_CUDA = 9,        /* a CUDA runtime call or a launch failed         */
+  COOT_ERR_TIMEOUT = 10,    /* a bounded device-side wait gave up             */
+  COOT_ERR_NOT_INIT = 11,   /* coot_init has not been called                  */
+  COOT_ERR_WORKSPACE = 12   /* workspace missing or too small                 */
+} coot_status;
+
+/* Storage types.  Arithmetic happens in the tree's compute type (FP32 or
+ * FP64); BF16 / FP16 elements are widened exactly on load and rounded to
+ * nearest-even on store (the paper's fused conversion, Section 7). */
+typedef enum coot_dtype {
+  COOT_F32 = 0,
+  COOT_BF16 = 1,
+  COOT_F16 = 2,
+  COOT_F64 = 3
+} coot_dtype;
+
+/* A column-major matrix in device memory: element (i, j), 0 <= i < n_rows,
+ * 0 <= j < n_cols, lives at ((T*)ptr)[i + j * ld] with T the storage type.
+ * ld >= max(n_rows, 1).  A vector is an n x 1 (column) or 1 x n (row)
+ * matrix (Table 1, Col / Row).  n_rows * n_cols == 0 is an empty object. */
+typedef struct coot_mat {
+  void* ptr;
+  int32_t dtype; /* coot_dtype */
+  int32_t reserved; /* must be 0 */
+  int64_t n_rows;
+  int64_t n_cols;
+  int64_t ld;
+} coot_mat;
+
+/* ------------------------------------------------------------------------
+ * Serialised expression tree (little-endian), the run-time form of the
+ * paper's expression types (eOp / eGlue, Section 7):
+ *
+ *   header, 16 bytes:
+ *     char     magic[4] = "COOT"
+ *     uint16_t version = 1
+ *     uint16_t n_nodes        1..64
+ *     uint8_t  n_inputs       1..4   number of input slots (operands passed)
+ *     uint8_t  compute        0 = FP32, 3 = FP64 arithmetic
+ *     uint16_t reserved = 0
+ *     uint32_t reserved = 0
+ *   node k (k = 0 .. n_nodes-1), 16 bytes at offset 16 + 16 k:
+ *     uint8_t  op             a coot_op below
+ *     uint8_t  reserved = 0
+ *     uint16_t a              operand: an earlier node (a < k) or, for
+ *                             COOT_OP_INPUT, the input slot (< n_inputs)
+ *     uint16_t b              second operand of binary nodes (b < k), else 0
+ *     uint16_t reserved = 0
+ *     double   imm            value of COOT_OP_CONST, else ignored (write 0)
+ *
+ * The last node is the root.  Nodes may be shared (a DAG).  Immediates are
+ * rounded to the compute type before use.  Scalar forms of Table 2
+ * ("A + k", "k - A", "A * k", ...) are binary nodes with a constant operand.
+ * ---------------------------------------------------------------------- */
+typedef enum coot_op {
+  COOT_OP_INPUT = 0,  /* input slot a                                      */
+  COOT_OP_CONST = 1,  /* scalar imm                                        */
+  COOT_OP_NEG = 2,    /* -a                                                */
+  COOT_OP_ABS = 3,    /* |a|                                               */
+  COOT_OP_EXP = 4,    /* exp(a)      Table 7                               */
+  COOT_OP_LOG = 5,    /* log(a)      Table 7 (natural logarithm)           */
+  COOT_OP_SQRT = 6,   /* sqrt(a)     Table 7                               */
+  COOT_OP_SQUARE = 7, /* a * a       Table 7                               */
+  COOT_OP_ADD = 8,    /* a + b       Table 2                               */
+  COOT_OP_SUB = 9,    /* a - b       Table 2                               */
+  COOT_OP_MUL = 10,   /* a % b       Table 2, element-wise (Schur) product */
+  COOT_OP_DIV = 11    /* a / b       Table 2, element-wise division        */
+} coot_op;
+
+#define COOT_TREE_MAX_NODES 64
+#define COOT_TREE_MAX_INPUTS 4
+
+/* Reduction heads for coot_expr_reduce: one result per set bit, written to
+ * out_dev[] in increasing bit order, as FP64. */
+#define COOT_HEAD_SUM    (1u << 0) /* sum of all elements (accu, Table 5)     */
+#define COOT_HEAD_SUMSQ  (1u << 1) /* sum of squares                           */
+#define COOT_HEAD_NORM2  (1u << 2) /* sqrt(sum of squares) (norm "fro" / 2)    */
+#define COOT_HEAD_SUMABS (1u << 3) /* sum of magnitudes (vector norm p = 1)    */
+#define COOT_HEAD_MIN    (1u << 4) /* smallest element (NaN propagates)        */
+#define COOT_HEAD_MAX    (1u << 5) /* largest element (NaN propagates)         */
+#define COOT_HEAD_MINABS (1u << 6) /* smallest magnitude (norm p = "-inf")     */
+#define COOT_HEAD_MAXABS (1u << 7) /* largest magnitude (norm p = "inf")       */
+#define COOT_HEAD_ALL    0xFFu
+
+/* norm(A, p) selectors (Table 5): p = 1, 2, or one of these. */
+#define COOT_NORM_INF (-1)
+#define COOT_NORM_NEG_INF (-2)
+#define COOT_NORM_FRO (-3)
+
+/* ------------------------------------------------------------------------
+ * Set-up
+ * ---------------------------------------------------------------------- */
+
+/* Select `device` (cudaSetDevice) and prepare the kernel cache; cf. the
+ * paper's coot_init(backend, print_info, device) (Section 2).  flags: bit 0
+ * = print device information to stderr.  Safe to call again; returns
+ * COOT_ERR_CUDA if the device cannot be used. */
+coot_status coot_init(int device, unsigned flags);
+
+/* Drop every cached kernel module (not the on-disk cache). */
+coot_status coot_finalize(void);
+
+/* Message for the last failing call on this thread ("" if none).  The
+ * pointer stays valid until the next call on this thread. */
+const char* coot_last_error(void);
+
+/* Short name of a status code. */
+const char* coot_status_string(coot_status s);
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+int coot_version(void);
+
+/* Bytes of workspace that suffice for every call on operands with at most
+ * `max_rows` rows (any number of columns).  Host-only. */
+coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
+
+/* Validate a serialised tree without a GPU: on success *n_inputs receives
+ * the tree's input count, *compute its compute dtype (COOT_F32 or COOT_F64)
+ * and *hash a 64-bit FNV-1a digest of the bytes (the kernel-cache key).
+ * Any of the out pointers may be NULL.  Host-only. */
+coot_status coot_tree_check(const uint8_t* tree, size_t tree_len, int* n_inputs,
+                            int* compute, uint64_t* hash);
+
+/* Compile the kernel of a tree with NVRTC for `arch` (e.g. "sm_103a")
+ * without loading it (no GPU needed); *cubin_bytes receives the size of
+ * the result.  kind as for coot_tree_source; in_dtype / out_dtype are the
+ * storage types of every input and of the output; heads as for
+ * coot_expr_reduce.  Host-only; for build checks and tests. */
+coot_status coot_tree_compile(const uint8_t* tree, size_t tree_len, int kind, int in_dtype,
+                              int out_dtype, unsigned heads, const char* arch,
+                              size_t* cubin_bytes);
+
+/* Write the CUDA source generated for a tree into buf (NUL-terminated,
+ * truncated to buf_len) and its full length to *len.  kind: 0 = element-wise
+ * evaluation, 1 = full reduction, 2 = column sums, 3 = row sums,
+ * 4 = batched evaluation; every input and the output FP32.  Host-only;
+ * for inspection and tests. */
+coot_status coot_tree_source(const uint8_t* tree, size_t tree_len, int kind, char* buf,
+                             size_t buf_len, size_t* len);
+
+/* ------------------------------------------------------------------------
+ * Evaluation.  `tree`/`tree_len` are a host buffer with the serialised
+ * tree; `in` is a host array of n_in device matrices (n_in == the tree's
+ * n_inputs), all with the same n_rows and n_cols (element-wise operations
+ * need equal sizes, Table 2).
+ * ---------------------------------------------------------------------- */
+
+/* out = tree(in...) element by element (delayed evaluation at assignment,
+ * Section 7; fused type conversion into out's storage type).  out must have
+ * the inputs' shape.  Empty shapes are a no-op. */
+coot_status coot_expr_eval(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                           const coot_mat* out, void* ws, size_t ws_bytes, void* stream);
+
+/* out_dev[0] = accu(tree(in...)) = sum of all elements (Table 5), FP64.
+ * Empty -> 0. */
+coot_status coot_accu(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                      double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* sum(tree(in...), dim) (Table 6): dim = 0 -> the sum of each column, out
+ * is 1 x n_cols; dim = 1 -> the sum of each row, out is n_rows x 1.  out may
+ * be any storage type (sums are formed in FP64 across blocks and rounded
+ * once).  out must not overlap an input. */
+coot_status coot_sum_dim(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                         int dim, const coot_mat* out, void* ws, size_t ws_bytes, void* stream);
+
+/* out_dev[0] = dot(a, b) = sum_i a_i * b_i over column-major element order;
+ * a and b need equal element counts, not equal shapes (Table 5).  FP32
+ * products (FP64 if either operand is FP64). */
+coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* out_dev[0] = norm(tree(in...), p) (Table 5).  p = 2 on a vector or
+ * COOT_NORM_FRO on anything: sqrt of the sum of squares; p = 1: sum of
+ * magnitudes; COOT_NORM_INF / COOT_NORM_NEG_INF: largest / smallest
+ * magnitude (vectors).  p = 2 of a matrix is the spectral norm and returns
+ * COOT_ERR_UNSUPPORTED.  Empty -> 0. */
+coot_status coot_norm(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in, int p,
+                      double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* out_dev[0] = min, out_dev[1] = max over all elements of tree(in...)
+ * (Table 6, both dimensions).  Element values are in the compute type; a
+ * NaN anywhere makes both results NaN.  Empty -> COOT_ERR_EMPTY. */
+coot_status coot_minmax(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                        double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Several reductions of one tree in ONE pass over the inputs, optionally
+ * also storing the element values: `heads` is a mask of COOT_HEAD_* bits;
+ * out_dev receives one FP64 per set bit in increasing bit order; `out` (may
+ * be NULL) receives the element-wise values as coot_expr_eval would.
+ * heads = 0 with out != NULL is coot_expr_eval. */
+coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                             unsigned heads, const coot_mat* out, double* out_dev, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Unfused baseline: the paper's own evaluation strategy, one kernel launch
+ * per operator node with each intermediate result in an HBM temporary
+ * (Section 7: every apply() launches at least one kernel; the last node
+ * writes into the destination with its type conversion fused).  Kept to
+ * measure what fusion buys on the same GPU.
+ * ---------------------------------------------------------------------- */
+
+/* *n_tmp = number of temporaries coot_unfused_eval needs: each holds
+ * n_rows * n_cols values of the tree's compute type.  Host-only. */
+coot_status coot_unfused_tmp_count(const uint8_t* tree, size_t tree_len, int* n_tmp);
+
+/* out = tree(in...) evaluated node by node.  tmp: device buffer of at least
+ * n_tmp * n_rows * n_cols * sizeof(compute type) bytes (caller-owned). */
+coot_status coot_unfused_eval(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                              const coot_mat* out, void* tmp, size_t tmp_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COOT_H */

@@ -1,0 +1,250 @@
+"""Fused element-wise expression + reduction engine for GB300 (sm_103a).
+
+A thin binding over libcoot.so (include/coot.h).  PyTorch supplies device
+memory and streams; every computation happens inside the library's CUDA
+kernels.  The functions below carry the ABI's names and take torch-backed
+`Mat` operands:
+
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300.expr import var, exp
+    x, z = var(0), var(1)
+    coot.coot_init(0)
+    coot.coot_expr_eval((2 * x + 3 * z).tree(), [X, Z], Y)    # Y = 2X + 3Z
+    s = coot.coot_accu((x % z).tree(), [X, Z])                # accu(X % Z)
+
+There is no CPU path: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+from . import _abi
+from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
+                   HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM, HEAD_SUMABS, HEAD_SUMSQ,
+                   CootError, coot_mat)
+from .expr import Expr, abs_, const, exp, log, serialize, sqrt, square, var
+
+__all__ = [
+    "Mat", "Workspace", "CootError", "coot_init", "coot_finalize", "coot_workspace_size", "coot_tree_check",
+    "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
+    "coot_norm", "coot_minmax", "coot_expr_reduce", "coot_unfused_eval", "coot_unfused_tmp_count",
+    "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "serialize",
+]
+
+_TORCH_DTYPES = None
+
+
+def _dtype_code(t) -> int:
+    global _TORCH_DTYPES
+    import torch
+    if _TORCH_DTYPES is None:
+        _TORCH_DTYPES = {torch.float32: COOT_F32, torch.bfloat16: COOT_BF16, torch.float16: COOT_F16,
+                         torch.float64: COOT_F64}
+    try:
+        return _TORCH_DTYPES[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported element type {t.dtype}") from None
+
+
+@dataclass
+class Mat:
+    """A column-major n_rows x n_cols matrix over torch storage: element
+    (i, j) is buf[offset + i + j * ld] (buf flattened)."""
+    buf: object
+    n_rows: int
+    n_cols: int
+    ld: int
+    offset: int = 0
+
+    @staticmethod
+    def of(t, n_rows: int | None = None, n_cols: int | None = None, ld: int | None = None) -> "Mat":
+        """Wrap a tensor.  1-D: an n x 1 column (or the given shape);
+        2-D: must be column-major (stride(0) == 1), e.g. torch.empty(c, r).t()."""
+        if t.dim() == 2 and n_rows is None:
+            if t.shape[0] > 1 and t.stride(0) != 1:
+                raise ValueError("2-D tensors must be column-major (stride(0) == 1)")
+            return Mat(t, t.shape[0], t.shape[1], max(t.stride(1), t.shape[0], 1), 0)
+        if n_rows is None:
+            n_rows, n_cols = t.numel(), 1
+        n_cols = 1 if n_cols is None else n_cols
+        ld = max(n_rows, 1) if ld is None else ld
+        return Mat(t, n_rows, n_cols, ld, 0)
+
+    def c(self) -> coot_mat:
+        t = self.buf
+        ptr = t.data_ptr() + self.offset * t.element_size()
+        return coot_mat(ptr, _dtype_code(t), 0, self.n_rows, self.n_cols, self.ld)
+
+
+def _mats(ms):
+    arr = (coot_mat * len(ms))(*[m.c() for m in ms])
+    return arr, len(ms)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Workspace:
+    """Zero-filled device workspace sized by coot_workspace_size."""
+
+    def __init__(self, max_rows: int, device="cuda"):
+        import torch
+        self.bytes = coot_workspace_size(max_rows)
+        self.buf = torch.zeros(self.bytes, dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+
+_default_ws = {}
+
+
+def _ws(ws, rows):
+    if ws is not None:
+        return ws
+    import torch
+    dev = torch.cuda.current_device()
+    cur = _default_ws.get(dev)
+    if cur is None or cur.bytes < coot_workspace_size(rows):
+        cur = Workspace(max(rows, 1 << 14), device=f"cuda:{dev}")
+        _default_ws[dev] = cur
+    return cur
+
+
+# ---------------------------------------------------------------- set-up / host-only
+
+def coot_init(device: int = 0, flags: int = 0) -> None:
+    _abi.call("coot_init", device, flags)
+
+
+def coot_finalize() -> None:
+    _abi.call("coot_finalize")
+
+
+def coot_workspace_size(max_rows: int) -> int:
+    n = ctypes.c_size_t()
+    _abi.call("coot_workspace_size", max_rows, ctypes.byref(n))
+    return n.value
+
+
+def coot_tree_check(tree: bytes):
+    n_in, comp, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
+    _abi.call("coot_tree_check", tree, len(tree), ctypes.byref(n_in), ctypes.byref(comp), ctypes.byref(h))
+    return n_in.value, comp.value, h.value
+
+
+def coot_tree_source(tree: bytes, kind: int = 0) -> str:
+    n = ctypes.c_size_t()
+    _abi.call("coot_tree_source", tree, len(tree), kind, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _abi.call("coot_tree_source", tree, len(tree), kind, buf, n.value + 1, ctypes.byref(n))
+    return buf.value.decode()
+
+
+def coot_tree_compile(tree: bytes, kind: int = 0, in_dtype: int = COOT_F32, out_dtype: int = COOT_F32,
+                      heads: int = 0, arch: str = "sm_103a") -> int:
+    n = ctypes.c_size_t()
+    _abi.call("coot_tree_compile", tree, len(tree), kind, in_dtype, out_dtype, heads, arch.encode(),
+              ctypes.byref(n))
+    return n.value
+
+
+def coot_unfused_tmp_count(tree: bytes) -> int:
+    n = ctypes.c_int()
+    _abi.call("coot_unfused_tmp_count", tree, len(tree), ctypes.byref(n))
+    return n.value
+
+
+# ---------------------------------------------------------------- device calls
+
+def _result(out_dev, n):
+    import torch
+    if out_dev is None:
+        out_dev = torch.empty(n, dtype=torch.float64, device="cuda")
+    return out_dev
+
+
+def coot_expr_eval(tree: bytes, ins, out: Mat, ws=None, stream=None) -> None:
+    arr, n = _mats(ins)
+    o = out.c()
+    _abi.call("coot_expr_eval", tree, len(tree), arr, n, ctypes.byref(o), None, 0, _stream(stream))
+
+
+def coot_expr_reduce(tree: bytes, ins, heads: int, out: Mat | None = None, out_dev=None, ws=None, stream=None):
+    """Several reductions (HEAD_* mask) in one pass; returns the FP64 device
+    tensor of results (one per set bit, increasing bit order)."""
+    arr, n = _mats(ins)
+    w = _ws(ws, 0)
+    res = _result(out_dev, bin(heads).count("1"))
+    o = ctypes.byref(out.c()) if out is not None else None
+    _abi.call("coot_expr_reduce", tree, len(tree), arr, n, heads, o, ctypes.c_void_p(res.data_ptr()), w.ptr,
+              w.bytes, _stream(stream))
+    return res
+
+
+def coot_accu(tree: bytes, ins, out_dev=None, ws=None, stream=None):
+    arr, n = _mats(ins)
+    w = _ws(ws, 0)
+    res = _result(out_dev, 1)
+    _abi.call("coot_accu", tree, len(tree), arr, n, ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
+              _stream(stream))
+    return res
+
+
+def coot_sum_dim(tree: bytes, ins, dim: int, out: Mat, ws=None, stream=None) -> None:
+    arr, n = _mats(ins)
+    w = _ws(ws, ins[0].n_rows if dim == 1 else 0)
+    o = out.c()
+    _abi.call("coot_sum_dim", tree, len(tree), arr, n, dim, ctypes.byref(o), w.ptr, w.bytes, _stream(stream))
+
+
+def coot_dot(a: Mat, b: Mat, out_dev=None, ws=None, stream=None):
+    w = _ws(ws, 0)
+    res = _result(out_dev, 1)
+    ca, cb = a.c(), b.c()
+    _abi.call("coot_dot", ctypes.byref(ca), ctypes.byref(cb), ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
+              _stream(stream))
+    return res
+
+
+def coot_norm(tree: bytes, ins, p, out_dev=None, ws=None, stream=None):
+    """p: 1, 2, "inf", "-inf" or "fro"."""
+    code = {"inf": COOT_NORM_INF, "-inf": COOT_NORM_NEG_INF, "fro": COOT_NORM_FRO}.get(p, p)
+    arr, n = _mats(ins)
+    w = _ws(ws, 0)
+    res = _result(out_dev, 1)
+    _abi.call("coot_norm", tree, len(tree), arr, n, int(code), ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
+              _stream(stream))
+    return res
+
+
+def coot_minmax(tree: bytes, ins, out_dev=None, ws=None, stream=None):
+    arr, n = _mats(ins)
+    w = _ws(ws, 0)
+    res = _result(out_dev, 2)
+    _abi.call("coot_minmax", tree, len(tree), arr, n, ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
+              _stream(stream))
+    return res
+
+
+def coot_unfused_eval(tree: bytes, ins, out: Mat, tmp=None, stream=None) -> None:
+    import torch
+    arr, n = _mats(ins)
+    k = coot_unfused_tmp_count(tree)
+    _, comp, _ = coot_tree_check(tree)
+    esize = 8 if comp == COOT_F64 else 4
+    need = k * ins[0].n_rows * ins[0].n_cols * esize
+    if tmp is None or tmp.numel() * tmp.element_size() < need:
+        tmp = torch.empty(max(need, 16), dtype=torch.uint8, device="cuda")
+    o = out.c()
+    _abi.call("coot_unfused_eval", tree, len(tree), arr, n, ctypes.byref(o), ctypes.c_void_p(tmp.data_ptr()),
+              tmp.numel() * tmp.element_size(), _stream(stream))
+    return tmp

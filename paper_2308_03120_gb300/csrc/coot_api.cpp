@@ -1,0 +1,569 @@
+// The C ABI (coot.h): argument checks, launch-shape selection and kernel
+// launches.  Everything that runs per element runs in the generated
+// kernels; this file only decides which kernel and which grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "coot_internal.h"
+
+namespace coot {
+
+static thread_local std::string g_err;
+
+coot_status fail(coot_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+void clear_error() { g_err.clear(); }
+
+coot_status init_device(int dev, unsigned flags);               // coot_jit.cpp
+coot_status compile_only(const std::string& source, const std::string& arch, size_t* bytes);
+
+static int dtype_size(int dt) {
+  switch (dt) {
+    case COOT_F32: return 4;
+    case COOT_BF16: return 2;
+    case COOT_F16: return 2;
+    case COOT_F64: return 8;
+  }
+  return 0;
+}
+
+static coot_status check_mat(const coot_mat* m, const char* what) {
+  if (m == nullptr) return fail(COOT_ERR_INVALID_ARG, std::string(what) + " is NULL");
+  if (dtype_size(m->dtype) == 0) return fail(COOT_ERR_DTYPE, std::string(what) + ": unknown dtype");
+  if (m->reserved != 0) return fail(COOT_ERR_INVALID_ARG, std::string(what) + ": reserved field is not 0");
+  if (m->n_rows < 0 || m->n_cols < 0) return fail(COOT_ERR_INVALID_ARG, std::string(what) + ": negative size");
+  if (m->ld < std::max<int64_t>(m->n_rows, 1)) return fail(COOT_ERR_INVALID_ARG, std::string(what) + ": ld < n_rows");
+  if (m->n_rows > 0 && m->n_cols > 0 && m->ptr == nullptr)
+    return fail(COOT_ERR_INVALID_ARG, std::string(what) + ": NULL data pointer");
+  if (m->n_rows > (int64_t(1) << 40) || m->n_cols > (int64_t(1) << 40) || m->ld > (int64_t(1) << 40))
+    return fail(COOT_ERR_INVALID_ARG, std::string(what) + ": size too large");
+  return COOT_OK;
+}
+
+static int64_t n_elem(const coot_mat& m) { return m.n_rows * m.n_cols; }
+
+// [first, last) byte range a matrix touches
+static void byte_range(const coot_mat& m, uintptr_t* b, uintptr_t* e) {
+  const uintptr_t base = (uintptr_t)m.ptr;
+  *b = base;
+  *e = base + (uintptr_t)((m.n_cols - 1) * m.ld + m.n_rows) * dtype_size(m.dtype);
+}
+
+static bool same_mat(const coot_mat& a, const coot_mat& b) {
+  return a.ptr == b.ptr && a.dtype == b.dtype && a.n_rows == b.n_rows && a.n_cols == b.n_cols && a.ld == b.ld;
+}
+
+// Tree, operand count, operand checks and equal shapes.
+static coot_status check_operands(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, Tree* t) {
+  coot_status s = parse_tree(tree, len, t);
+  if (s != COOT_OK) return s;
+  if (in == nullptr) return fail(COOT_ERR_INVALID_ARG, "inputs are NULL");
+  if (n_in != t->n_inputs)
+    return fail(COOT_ERR_INVALID_ARG, "tree has " + std::to_string(t->n_inputs) + " inputs, " +
+                                          std::to_string(n_in) + " given");
+  for (int i = 0; i < n_in; ++i) {
+    s = check_mat(&in[i], "input");
+    if (s != COOT_OK) return s;
+    if (in[i].n_rows != in[0].n_rows || in[i].n_cols != in[0].n_cols)
+      return fail(COOT_ERR_SHAPE, "element-wise operands need equal sizes: input " + std::to_string(i) + " is " +
+                                      std::to_string(in[i].n_rows) + "x" + std::to_string(in[i].n_cols) +
+                                      ", input 0 is " + std::to_string(in[0].n_rows) + "x" +
+                                      std::to_string(in[0].n_cols));
+  }
+  return COOT_OK;
+}
+
+// Output aliasing: identical to an input is allowed (and disables the
+// non-coherent load path), any other overlap is an error.
+static coot_status check_alias(const coot_mat& out, const coot_mat* in, int n_in, bool allow_identical, bool* aliased) {
+  *aliased = false;
+  if (n_elem(out) == 0) return COOT_OK;
+  uintptr_t ob, oe;
+  byte_range(out, &ob, &oe);
+  for (int i = 0; i < n_in; ++i) {
+    if (n_elem(in[i]) == 0) continue;
+    uintptr_t ib, ie;
+    byte_range(in[i], &ib, &ie);
+    if (ob < ie && ib < oe) {
+      if (allow_identical && same_mat(out, in[i])) {
+        *aliased = true;
+      } else {
+        return fail(COOT_ERR_ALIAS, "output overlaps input " + std::to_string(i) + " without being identical to it");
+      }
+    }
+  }
+  return COOT_OK;
+}
+
+// Operands as the kernels see them: a 2-D column-major view (n_rows x
+// n_cols, per-operand ld).  When every operand is dense (ld == n_rows or a
+// single column) the whole object is one long column.
+struct View {
+  const void* ptr[5];
+  int64_t ld[5];
+  int dtype[5];
+  int n = 0;  // operands (inputs, then the stored output if any)
+  int64_t n_rows = 0, n_cols = 0;
+};
+
+static View make_view(const coot_mat* in, int n_in, const coot_mat* out) {
+  View v;
+  v.n_rows = in[0].n_rows;
+  v.n_cols = in[0].n_cols;
+  for (int i = 0; i < n_in; ++i) {
+    v.ptr[v.n] = in[i].ptr;
+    v.ld[v.n] = in[i].ld;
+    v.dtype[v.n] = in[i].dtype;
+    ++v.n;
+  }
+  if (out) {
+    v.ptr[v.n] = out->ptr;
+    v.ld[v.n] = out->ld;
+    v.dtype[v.n] = out->dtype;
+    ++v.n;
+  }
+  bool dense = true;
+  for (int i = 0; i < v.n; ++i) dense = dense && (v.ld[i] == v.n_rows || v.n_cols <= 1);
+  if (dense && v.n_cols > 1) {
+    v.n_rows = v.n_rows * v.n_cols;
+    v.n_cols = 1;
+    for (int i = 0; i < v.n; ++i) v.ld[i] = v.n_rows;
+  }
+  return v;
+}
+
+// Largest vector width (elements) with every access aligned: at most 16
+// bytes per access for the widest operand, every base pointer aligned to
+// the access, and every ld a multiple of it when there are several columns.
+static int pick_vec(const View& v, int max_vec = 8) {
+  int widest = 1;
+  for (int i = 0; i < v.n; ++i) widest = std::max(widest, dtype_size(v.dtype[i]));
+  for (int vec = max_vec; vec > 1; vec >>= 1) {
+    if (vec * widest > 16) continue;
+    bool ok = true;
+    for (int i = 0; i < v.n && ok; ++i) {
+      ok = ((uintptr_t)v.ptr[i] % (uintptr_t)(vec * dtype_size(v.dtype[i]))) == 0;
+      if (v.n_cols > 1) ok = ok && (v.ld[i] % vec == 0);
+    }
+    if (ok) return vec;
+  }
+  return 1;
+}
+
+// ------------------------------------------------------------ launch policy
+
+struct Launch {
+  int vec = 1, unroll = 1, block = 256;
+};
+
+static Launch heuristic(int kind, int n_in, const View& v) {
+  Launch l;
+  l.vec = pick_vec(v);
+  l.block = 256;
+  if (kind == KIND_ROWSUM) {
+    l.unroll = n_in >= 3 ? 2 : 4;
+  } else {
+    l.unroll = std::max(1, std::min(4, 8 / std::max(1, n_in)));
+  }
+  return l;
+}
+
+static void fill_io(coot_params_host* p, const View& v, int n_in) {
+  std::memset(p, 0, sizeof *p);
+  for (int i = 0; i < n_in; ++i) {
+    p->in[i] = v.ptr[i];
+    p->ld_in[i] = v.ld[i];
+  }
+  for (int i = n_in; i < 4; ++i) p->ld_in[i] = 1;
+  p->n_rows = v.n_rows;
+  p->n_cols = v.n_cols;
+}
+
+static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, int block, coot_params_host* p,
+                          void* stream) {
+  int64_t grid = (int64_t)device().sm_count * std::max(1, c->max_blocks_per_sm);
+  grid = std::min(grid, std::max<int64_t>(units, 1));
+  grid = std::min(grid, max_grid);
+  grid = std::max<int64_t>(grid, 1);
+  void* args[] = {p};
+  cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(block), args, 0,
+                                   (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return COOT_OK;
+}
+
+static int popcount(unsigned m) {
+  int k = 0;
+  for (; m; m &= m - 1) ++k;
+  return k;
+}
+
+static int tile_rows(const Launch& l) { return l.block * l.vec * l.unroll; }
+
+// Element-wise evaluation and/or full reductions of one tree.
+static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, unsigned heads, const coot_mat* out,
+                                  double* res, void* ws, size_t ws_bytes, void* stream) {
+  const bool store = out != nullptr;
+  const int64_t n = n_elem(in[0]);
+  if (heads) {
+    if (res == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
+    if (n == 0) {
+      if (heads & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
+      cudaError_t e = cudaMemsetAsync(res, 0, sizeof(double) * popcount(heads), (cudaStream_t)stream);
+      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+      return COOT_OK;
+    }
+    if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * popcount(heads))
+      return fail(COOT_ERR_WORKSPACE, "reductions need a workspace (coot_workspace_size)");
+  } else if (n == 0) {
+    return COOT_OK;
+  }
+  bool aliased = false;
+  if (store) {
+    coot_status s = check_mat(out, "output");
+    if (s != COOT_OK) return s;
+    if (out->n_rows != in[0].n_rows || out->n_cols != in[0].n_cols)
+      return fail(COOT_ERR_SHAPE, "output shape differs from the operands'");
+    s = check_alias(*out, in, n_in, true, &aliased);
+    if (s != COOT_OK) return s;
+  }
+  const View v = make_view(in, n_in, store ? out : nullptr);
+  const int kind = heads ? (store ? KIND_MAP : KIND_REDUCE) : KIND_MAP;
+  const Launch l = heuristic(kind, n_in, v);
+  KernelSpec spec;
+  spec.kind = kind;
+  for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
+  spec.out_dtype = store ? out->dtype : 0;
+  spec.store = store;
+  spec.heads = heads;
+  spec.vec = l.vec;
+  spec.unroll = l.unroll;
+  spec.block = l.block;
+  spec.nc = !aliased;
+  const Compiled* c = nullptr;
+  coot_status s = get_kernel(generate_source(t, spec), spec, &c);
+  if (s != COOT_OK) return s;
+  coot_params_host p;
+  fill_io(&p, v, n_in);
+  if (store) {
+    p.out = v.ptr[n_in] ? const_cast<void*>(v.ptr[n_in]) : nullptr;
+    p.ld_out = v.ld[n_in];
+  }
+  p.ws = (unsigned char*)ws;
+  p.res = res;
+  const int64_t tile = tile_rows(l);
+  const int64_t units = ((v.n_rows + tile - 1) / tile) * v.n_cols;
+  int64_t max_grid = INT32_MAX;
+  if (heads) {
+    const int64_t fit = (int64_t)((ws_bytes - COOT_WS_PARTIALS_OFF) / (sizeof(double) * popcount(heads)));
+    max_grid = std::min<int64_t>(COOT_MAX_GRID, fit);
+  }
+  return launch(c, units, max_grid, l.block, &p, stream);
+}
+
+static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int dim, const coot_mat* out, void* ws,
+                               size_t ws_bytes, void* stream) {
+  coot_status s = check_mat(out, "output");
+  if (s != COOT_OK) return s;
+  const int64_t R = in[0].n_rows, Cn = in[0].n_cols;
+  if (dim == 0) {
+    if (out->n_rows != 1 || out->n_cols != Cn)
+      return fail(COOT_ERR_SHAPE, "sum(dim=0) output must be 1 x n_cols");
+  } else if (dim == 1) {
+    if (out->n_rows != R || out->n_cols != 1)
+      return fail(COOT_ERR_SHAPE, "sum(dim=1) output must be n_rows x 1");
+  } else {
+    return fail(COOT_ERR_INVALID_ARG, "dim must be 0 or 1");
+  }
+  bool aliased = false;
+  s = check_alias(*out, in, n_in, false, &aliased);
+  if (s != COOT_OK) return s;
+  if (n_elem(*out) == 0) return COOT_OK;
+  // the element layout of the operands; the output is addressed separately
+  View v;
+  v.n_rows = R;
+  v.n_cols = Cn;
+  for (int i = 0; i < n_in; ++i) {
+    v.ptr[i] = in[i].ptr;
+    v.ld[i] = in[i].ld;
+    v.dtype[i] = in[i].dtype;
+  }
+  v.n = n_in;
+  const int kind = dim == 0 ? KIND_COLSUM : KIND_ROWSUM;
+  Launch l = heuristic(kind, n_in, v);
+  const Device& d = device();
+  KernelSpec spec;
+  spec.kind = kind;
+  for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
+  spec.out_dtype = out->dtype;
+  spec.vec = l.vec;
+  spec.unroll = l.unroll;
+  spec.block = l.block;
+  spec.nc = true;
+  const Compiled* c = nullptr;
+  s = get_kernel(generate_source(t, spec), spec, &c);
+  if (s != COOT_OK) return s;
+  coot_params_host p;
+  fill_io(&p, v, n_in);
+  p.out = out->ptr;
+  p.ld_out = out->ld;
+  p.ws = (unsigned char*)ws;
+  const int64_t resident = (int64_t)d.sm_count * std::max(1, c->max_blocks_per_sm);
+  const size_t part_bytes = ws ? (ws_bytes > COOT_WS_PARTIALS_OFF ? ws_bytes - COOT_WS_PARTIALS_OFF : 0) : 0;
+  int64_t units;
+  if (dim == 0) {
+    // split tall columns over several blocks when there are too few columns
+    const int64_t tile = tile_rows(l);
+    int64_t S = 1;
+    if (Cn < resident && R > 4 * tile) {
+      S = std::min<int64_t>((resident + Cn - 1) / Cn, (R + tile - 1) / tile);
+      S = std::min<int64_t>(S, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(Cn, 1))) / 1);
+      if (Cn > COOT_WS_MAX_COUNTERS) S = 1;
+      S = std::max<int64_t>(S, 1);
+    }
+    int64_t rps = (R + S - 1) / S;
+    rps = ((rps + tile - 1) / tile) * tile;
+    if (S > 1) S = (R + rps - 1) / rps;
+    p.split = S;
+    p.rows_per_split = std::max<int64_t>(rps, 1);
+    units = Cn * S;
+  } else {
+    const int64_t panel = (int64_t)l.block * l.vec;
+    const int64_t n_panels = (R + panel - 1) / panel;
+    int64_t C = std::max<int64_t>(1, (2 * resident + n_panels - 1) / n_panels);
+    C = std::min<int64_t>(C, std::max<int64_t>(Cn, 1));
+    C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);
+    C = std::min<int64_t>(C, (int64_t)(part_bytes / (sizeof(double) * R)));
+    if (n_panels > COOT_WS_MAX_COUNTERS) C = 1;
+    C = std::max<int64_t>(C, 1);
+    p.split = C;
+    units = n_panels * C;
+  }
+  if (p.split > 1 && ws == nullptr) return fail(COOT_ERR_WORKSPACE, "split sums need a workspace");
+  return launch(c, units, INT32_MAX, l.block, &p, stream);
+}
+
+}  // namespace coot
+
+using namespace coot;
+
+extern "C" {
+
+coot_status coot_init(int dev, unsigned flags) {
+  clear_error();
+  return init_device(dev, flags);
+}
+
+coot_status coot_finalize(void) {
+  clear_error();
+  drop_kernels();
+  return COOT_OK;
+}
+
+const char* coot_last_error(void) { return g_err.c_str(); }
+
+const char* coot_status_string(coot_status s) {
+  switch (s) {
+    case COOT_OK: return "COOT_OK";
+    case COOT_ERR_INVALID_ARG: return "COOT_ERR_INVALID_ARG";
+    case COOT_ERR_BAD_TREE: return "COOT_ERR_BAD_TREE";
+    case COOT_ERR_SHAPE: return "COOT_ERR_SHAPE";
+    case COOT_ERR_DTYPE: return "COOT_ERR_DTYPE";
+    case COOT_ERR_ALIAS: return "COOT_ERR_ALIAS";
+    case COOT_ERR_EMPTY: return "COOT_ERR_EMPTY";
+    case COOT_ERR_UNSUPPORTED: return "COOT_ERR_UNSUPPORTED";
+    case COOT_ERR_COMPILE: return "COOT_ERR_COMPILE";
+    case COOT_ERR_CUDA: return "COOT_ERR_CUDA";
+    case COOT_ERR_TIMEOUT: return "COOT_ERR_TIMEOUT";
+    case COOT_ERR_NOT_INIT: return "COOT_ERR_NOT_INIT";
+    case COOT_ERR_WORKSPACE: return "COOT_ERR_WORKSPACE";
+  }
+  return "COOT_ERR_UNKNOWN";
+}
+
+int coot_version(void) { return 100; }
+
+coot_status coot_workspace_size(int64_t max_rows, size_t* bytes) {
+  clear_error();
+  if (bytes == nullptr || max_rows < 0) return fail(COOT_ERR_INVALID_ARG, "bad workspace query");
+  size_t part = (size_t)COOT_MAX_GRID * 8 * sizeof(double);
+  part = std::max(part, (size_t)COOT_MAX_ROW_CHUNKS * (size_t)max_rows * sizeof(double));
+  part = std::max(part, (size_t)COOT_WS_MAX_COUNTERS * 8 * sizeof(double));
+  *bytes = COOT_WS_PARTIALS_OFF + part;
+  return COOT_OK;
+}
+
+coot_status coot_tree_check(const uint8_t* tree, size_t len, int* n_inputs, int* compute, uint64_t* hash) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  if (n_inputs) *n_inputs = t.n_inputs;
+  if (compute) *compute = t.compute;
+  if (hash) *hash = t.hash;
+  return COOT_OK;
+}
+
+static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype, unsigned heads, KernelSpec* spec) {
+  if (kind < 0 || kind > 3) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..3");
+  if (dtype_size(in_dtype) == 0 || dtype_size(out_dtype) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
+  spec->kind = kind;
+  for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
+  spec->out_dtype = out_dtype;
+  spec->store = kind == KIND_MAP;
+  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE) ? heads : 0;
+  spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
+  spec->unroll = 2;
+  spec->block = 256;
+  return COOT_OK;
+}
+
+coot_status coot_tree_source(const uint8_t* tree, size_t len, int kind, char* buf, size_t buf_len, size_t* out_len) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  KernelSpec spec;
+  s = spec_for(t, kind, COOT_F32, COOT_F32, kind == KIND_REDUCE ? COOT_HEAD_SUM : 0, &spec);
+  if (s != COOT_OK) return s;
+  const std::string src = generate_source(t, spec);
+  if (out_len) *out_len = src.size();
+  if (buf && buf_len) {
+    const size_t n = std::min(buf_len - 1, src.size());
+    std::memcpy(buf, src.data(), n);
+    buf[n] = '\0';
+  }
+  return COOT_OK;
+}
+
+coot_status coot_tree_compile(const uint8_t* tree, size_t len, int kind, int in_dtype, int out_dtype, unsigned heads,
+                              const char* arch, size_t* cubin_bytes) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  if (arch == nullptr) return fail(COOT_ERR_INVALID_ARG, "arch is NULL");
+  KernelSpec spec;
+  s = spec_for(t, kind, in_dtype, out_dtype, heads, &spec);
+  if (s != COOT_OK) return s;
+  return compile_only(generate_source(t, spec), arch, cubin_bytes);
+}
+
+coot_status coot_expr_eval(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, const coot_mat* out,
+                           void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  if (out == nullptr) return fail(COOT_ERR_INVALID_ARG, "output is NULL");
+  return run_map_reduce(t, in, n_in, 0, out, nullptr, ws, ws_bytes, stream);
+}
+
+coot_status coot_expr_reduce(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, unsigned heads,
+                             const coot_mat* out, double* out_dev, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  if (heads & ~COOT_HEAD_ALL) return fail(COOT_ERR_INVALID_ARG, "unknown head bits");
+  if (heads == 0 && out == nullptr) return fail(COOT_ERR_INVALID_ARG, "nothing to compute");
+  return run_map_reduce(t, in, n_in, heads, out, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_accu(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
+                      size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  return run_map_reduce(t, in, n_in, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_minmax(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
+                        size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  return run_map_reduce(t, in, n_in, COOT_HEAD_MIN | COOT_HEAD_MAX, nullptr, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_norm(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int p, double* out_dev,
+                      void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  const bool is_vec = in[0].n_rows == 1 || in[0].n_cols == 1 || n_elem(in[0]) == 0;
+  unsigned head;
+  if (p == COOT_NORM_FRO || (p == 2 && is_vec)) {
+    head = COOT_HEAD_NORM2;
+  } else if (p == 2) {
+    return fail(COOT_ERR_UNSUPPORTED, "norm(A, 2) of a matrix is the spectral norm (needs an SVD)");
+  } else if (p == 1 || p == COOT_NORM_INF || p == COOT_NORM_NEG_INF) {
+    if (!is_vec) return fail(COOT_ERR_UNSUPPORTED, "norm p = 1 / inf / -inf is implemented for vectors");
+    head = p == 1 ? COOT_HEAD_SUMABS : (p == COOT_NORM_INF ? COOT_HEAD_MAXABS : COOT_HEAD_MINABS);
+  } else {
+    return fail(COOT_ERR_INVALID_ARG, "p must be 1, 2, COOT_NORM_INF, COOT_NORM_NEG_INF or COOT_NORM_FRO");
+  }
+  return run_map_reduce(t, in, n_in, head, nullptr, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_sum_dim(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int dim, const coot_mat* out,
+                         void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  return run_sum_dim(t, in, n_in, dim, out, ws, ws_bytes, stream);
+}
+
+coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  coot_status s = check_mat(a, "a");
+  if (s != COOT_OK) return s;
+  s = check_mat(b, "b");
+  if (s != COOT_OK) return s;
+  if (n_elem(*a) != n_elem(*b)) return fail(COOT_ERR_SHAPE, "dot needs equal element counts");
+  coot_mat m[2] = {*a, *b};
+  if (a->n_rows != b->n_rows || a->n_cols != b->n_cols) {
+    // different shapes with equal counts: both must be dense to share one
+    // column-major element order
+    const bool da = a->ld == a->n_rows || a->n_cols <= 1;
+    const bool db = b->ld == b->n_rows || b->n_cols <= 1;
+    const bool ra = a->n_rows == 1 && a->ld != 1 && a->n_cols > 1;
+    const bool rb = b->n_rows == 1 && b->ld != 1 && b->n_cols > 1;
+    if (!da || !db || ra || rb)
+      return fail(COOT_ERR_UNSUPPORTED, "dot of differently shaped strided operands");
+    for (auto& x : m) {
+      x.n_rows = n_elem(x);
+      x.n_cols = 1;
+      x.ld = std::max<int64_t>(x.n_rows, 1);
+    }
+  }
+  // the tree x0 % x1 in FP32 (FP64 if either operand is FP64)
+  const bool f64 = a->dtype == COOT_F64 || b->dtype == COOT_F64;
+  uint8_t buf[16 + 3 * 16];
+  std::memset(buf, 0, sizeof buf);
+  std::memcpy(buf, "COOT", 4);
+  buf[4] = 1;
+  buf[6] = 3;
+  buf[8] = 2;
+  buf[9] = f64 ? COOT_F64 : COOT_F32;
+  buf[16 + 16] = COOT_OP_INPUT;
+  buf[16 + 16 + 2] = 1;
+  buf[16 + 32] = COOT_OP_MUL;
+  buf[16 + 32 + 4] = 1;
+  Tree t;
+  s = parse_tree(buf, sizeof buf, &t);
+  if (s != COOT_OK) return s;
+  return run_map_reduce(t, m, 2, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
+}
+
+}  // extern "C"

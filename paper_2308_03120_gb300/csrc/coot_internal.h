@@ -1,0 +1,110 @@
+// Internal declarations shared by the host-side translation units of
+// libcoot.so (tree parsing, code generation, run-time compilation, launch).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "coot.h"
+
+namespace coot {
+
+// ------------------------------------------------------------ errors
+
+// Records `msg` as the calling thread's last error and returns `s`.
+coot_status fail(coot_status s, const std::string& msg);
+void clear_error();
+
+// ------------------------------------------------------------ trees
+
+struct Node {
+  uint8_t op;
+  uint16_t a, b;
+  double imm;
+};
+
+struct Tree {
+  std::vector<Node> nodes;
+  int n_inputs = 0;
+  int compute = COOT_F32;  // COOT_F32 or COOT_F64
+  uint64_t hash = 0;       // FNV-1a of the serialised bytes
+};
+
+// Parses and validates the serialised form (format in coot.h).
+coot_status parse_tree(const uint8_t* buf, size_t len, Tree* out);
+
+// Kernel kinds (the prelude's COOT_KIND).
+enum Kind { KIND_MAP = 0, KIND_REDUCE = 1, KIND_COLSUM = 2, KIND_ROWSUM = 3, KIND_BATCHED = 4 };
+
+// Everything that selects one compiled kernel.
+struct KernelSpec {
+  int kind = KIND_MAP;
+  int in_dtype[4] = {0, 0, 0, 0};
+  int out_dtype = 0;
+  bool store = false;
+  unsigned heads = 0;
+  int vec = 1;
+  int unroll = 1;
+  int block = 256;
+  bool nc = true;  // inputs read through the non-coherent path
+};
+
+// Full CUDA source of one kernel: the prelude, the tree function and the
+// embedded device runtime.
+std::string generate_source(const Tree& t, const KernelSpec& spec);
+
+// ------------------------------------------------------------ JIT
+
+// A loaded kernel (cudaKernel_t) plus its static resource use.
+struct Compiled {
+  void* kernel = nullptr;
+  int max_blocks_per_sm = 0;
+  int num_regs = 0;
+};
+
+// Returns the compiled kernel for `source`, compiling it with NVRTC on a
+// miss (memory cache, then the on-disk cache, then NVRTC).
+coot_status get_kernel(const std::string& source, const KernelSpec& spec, const Compiled** out);
+void drop_kernels();
+
+// Device facts cached by coot_init.
+struct Device {
+  int id = -1;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  int max_threads_per_sm = 0;
+};
+const Device& device();
+bool initialised();
+
+uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull);
+
+}  // namespace coot
+
+// Launch-parameter block; identical layout to `coot_params` in jit_rt.cuh
+// (every field is 8 bytes).
+struct coot_params_host {
+  const void* in[4];
+  int64_t ld_in[4];
+  void* out;
+  int64_t ld_out;
+  int64_t n_rows;
+  int64_t n_cols;
+  int64_t split;
+  int64_t rows_per_split;
+  unsigned char* ws;
+  double* res;
+  const void* plan;
+  int64_t n_work;
+};
+static_assert(sizeof(coot_params_host) == 8 * 18, "coot_params layout");
+
+// Workspace layout (offsets in bytes), mirrored in jit_rt.cuh.
+#define COOT_WS_COUNTER_OFF 128
+#define COOT_WS_COUNTERS_OFF 256
+#define COOT_WS_PARTIALS_OFF 65536
+#define COOT_WS_MAX_COUNTERS ((COOT_WS_PARTIALS_OFF - COOT_WS_COUNTERS_OFF) / 4)
+#define COOT_MAX_GRID 4096
+#define COOT_MAX_ROW_CHUNKS 64

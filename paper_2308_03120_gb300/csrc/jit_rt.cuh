@@ -1,0 +1,686 @@
+// Device runtime of the fused expression kernels.
+//
+// This file is not compiled on its own: the library embeds it as a string
+// and, for every (tree, kind, storage types, launch shape), compiles it at
+// run time with NVRTC for the device's architecture (sm_103a on GB300),
+// after a prelude that defines
+//   COOT_KIND     0 element-wise evaluation (optionally with reductions),
+//                 1 full reductions only, 2 column sums, 3 row sums,
+//                 4 batched evaluation over a work list
+//   COOT_NIN      number of input slots (1..4)
+//   COOT_TI0..3   storage code of each input (0 FP32, 1 BF16, 2 FP16, 3 FP64)
+//   COOT_TO       storage code of the stored output
+//   COOT_STORE    1 if element values are stored
+//   COOT_HEADS    mask of reduction heads (COOT_HEAD_* in coot.h)
+//   COOT_REAL     float or double (the tree's compute type)
+//   COOT_VEC      elements per vector access, COOT_UNROLL vectors in flight
+//                 per thread and input, COOT_BLOCK threads per block
+//   COOT_NC       1 if inputs may be read through the non-coherent path
+// and the tree itself as `COOT_REAL coot_f(const COOT_REAL* x)`, one
+// straight-line function of the input values (the paper's expression type,
+// Section 7, instantiated for a single element).
+//
+// Every kernel is a persistent grid-stride loop over "units" (a tile of rows
+// of one column for evaluation and column sums, a panel of rows times a
+// range of columns for row sums), so any grid size covers any shape.
+// Reductions add in FP32 (or FP64) with TwoSum compensation per thread,
+// then combine per-thread results in FP64 through warp shuffles, shared
+// memory and one FP64 partial per block; the last block to finish combines
+// the partials in a fixed order, so a result does not depend on timing.
+
+typedef unsigned short coot_u16;
+typedef unsigned int coot_u32;
+typedef long long coot_i64;
+typedef unsigned long long coot_u64;
+
+// Launch parameters; every field is 8 bytes so the host-side copy of this
+// struct has the same layout.
+struct coot_params {
+  const void* in[4];
+  coot_i64 ld_in[4];
+  void* out;
+  coot_i64 ld_out;
+  coot_i64 n_rows;
+  coot_i64 n_cols;
+  coot_i64 split;           // column sums: blocks per column; row sums: column chunks
+  coot_i64 rows_per_split;  // column sums: rows per block when split > 1
+  unsigned char* ws;        // workspace (counters + partials)
+  double* res;              // reduction results
+  const void* plan;         // batched: work list
+  coot_i64 n_work;          // batched: number of work items
+};
+
+#define COOT_WS_COUNTER_OFF 128
+#define COOT_WS_COUNTERS_OFF 256
+#define COOT_WS_PARTIALS_OFF 65536
+
+#define COOT_HEAD_SUM (1u << 0)
+#define COOT_HEAD_SUMSQ (1u << 1)
+#define COOT_HEAD_NORM2 (1u << 2)
+#define COOT_HEAD_SUMABS (1u << 3)
+#define COOT_HEAD_MIN (1u << 4)
+#define COOT_HEAD_MAX (1u << 5)
+#define COOT_HEAD_MINABS (1u << 6)
+#define COOT_HEAD_MAXABS (1u << 7)
+
+#define COOT_WARPS (COOT_BLOCK / 32)
+#define COOT_INF_F __int_as_float(0x7f800000)
+#define COOT_INF_D __longlong_as_double(0x7ff0000000000000ll)
+
+// ---------------------------------------------------------------- storage
+
+template <int S> struct coot_st;
+template <> struct coot_st<0> { typedef float T; };
+template <> struct coot_st<1> { typedef coot_u16 T; };
+template <> struct coot_st<2> { typedef coot_u16 T; };
+template <> struct coot_st<3> { typedef double T; };
+
+template <int S>
+__device__ __forceinline__ COOT_REAL coot_to_real(typename coot_st<S>::T v) {
+  if constexpr (S == 0) {
+    return (COOT_REAL)v;
+  } else if constexpr (S == 1) {
+    // a BF16 number is the top half of the FP32 number with the same bits
+    return (COOT_REAL)__uint_as_float(((coot_u32)v) << 16);
+  } else if constexpr (S == 2) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(v));
+    return (COOT_REAL)f;
+  } else {
+    return (COOT_REAL)v;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ typename coot_st<S>::T coot_from_real(COOT_REAL v) {
+  if constexpr (S == 0) {
+    return (float)v;
+  } else if constexpr (S == 1) {
+    float f = (float)v;
+    coot_u16 h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return h;
+  } else if constexpr (S == 2) {
+    float f = (float)v;
+    coot_u16 h;
+    asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return h;
+  } else {
+    return (double)v;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ typename coot_st<S>::T coot_from_double(double v) {
+  if constexpr (S == 3) {
+    return v;
+  } else {
+    float f = (float)v;  // nearest FP32, then nearest storage value
+    if constexpr (S == 0) {
+      return f;
+    } else if constexpr (S == 1) {
+      coot_u16 h;
+      asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+      return h;
+    } else {
+      coot_u16 h;
+      asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+      return h;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- memory
+
+#if COOT_NC
+#define COOT_LD "ld.global.nc.L1::no_allocate"
+#else
+#define COOT_LD "ld.global"
+#endif
+
+__device__ __forceinline__ uint4 coot_ld16(const void* p) {
+  uint4 r;
+  asm(COOT_LD ".v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ uint2 coot_ld8(const void* p) {
+  uint2 r;
+  asm(COOT_LD ".v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ coot_u32 coot_ld4(const void* p) {
+  coot_u32 r;
+  asm(COOT_LD ".u32 %0, [%1];" : "=r"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ coot_u16 coot_ld2(const void* p) {
+  coot_u16 r;
+  asm(COOT_LD ".u16 %0, [%1];" : "=h"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ void coot_st16(void* p, uint4 v) {
+  asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};"
+               :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__device__ __forceinline__ void coot_st8(void* p, uint2 v) {
+  asm volatile("st.global.v2.u32 [%0], {%1, %2};" :: "l"(p), "r"(v.x), "r"(v.y) : "memory");
+}
+__device__ __forceinline__ void coot_st4(void* p, coot_u32 v) {
+  asm volatile("st.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void coot_st2(void* p, coot_u16 v) {
+  asm volatile("st.global.u16 [%0], %1;" :: "l"(p), "h"(v) : "memory");
+}
+
+// V consecutive elements of storage S at p (p aligned to V * sizeof(T))
+template <int S, int V>
+__device__ __forceinline__ void coot_vload(const typename coot_st<S>::T* p, COOT_REAL* x) {
+  typedef typename coot_st<S>::T T;
+  constexpr int B = V * (int)sizeof(T);
+  union {
+    uint4 q[B >= 16 ? B / 16 : 1];
+    uint2 d;
+    coot_u32 w;
+    coot_u16 h;
+    T e[V];
+  } u;
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) u.q[i] = coot_ld16((const char*)p + 16 * i);
+  } else if constexpr (B == 8) {
+    u.d = coot_ld8(p);
+  } else if constexpr (B == 4) {
+    u.w = coot_ld4(p);
+  } else {
+    u.h = coot_ld2(p);
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) x[v] = coot_to_real<S>(u.e[v]);
+}
+
+template <int S>
+__device__ __forceinline__ COOT_REAL coot_sload(const typename coot_st<S>::T* p) {
+  typedef typename coot_st<S>::T T;
+  if constexpr (sizeof(T) == 8) {
+    uint2 r = coot_ld8(p);
+    return coot_to_real<S>(__longlong_as_double(((coot_i64)r.y << 32) | r.x));
+  } else if constexpr (sizeof(T) == 4) {
+    return coot_to_real<S>(__uint_as_float(coot_ld4(p)));
+  } else {
+    return coot_to_real<S>(coot_ld2(p));
+  }
+}
+
+template <int S, int V>
+__device__ __forceinline__ void coot_vstore(typename coot_st<S>::T* p, const COOT_REAL* y) {
+  typedef typename coot_st<S>::T T;
+  constexpr int B = V * (int)sizeof(T);
+  union {
+    uint4 q[B >= 16 ? B / 16 : 1];
+    uint2 d;
+    coot_u32 w;
+    coot_u16 h;
+    T e[V];
+  } u;
+#pragma unroll
+  for (int v = 0; v < V; ++v) u.e[v] = coot_from_real<S>(y[v]);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) coot_st16((char*)p + 16 * i, u.q[i]);
+  } else if constexpr (B == 8) {
+    coot_st8(p, u.d);
+  } else if constexpr (B == 4) {
+    coot_st4(p, u.w);
+  } else {
+    coot_st2(p, u.h);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void coot_sstore(typename coot_st<S>::T* p, COOT_REAL y) {
+  *p = coot_from_real<S>(y);
+}
+
+template <int I> struct coot_in_code;
+template <> struct coot_in_code<0> { static constexpr int S = COOT_TI0; };
+template <> struct coot_in_code<1> { static constexpr int S = COOT_TI1; };
+template <> struct coot_in_code<2> { static constexpr int S = COOT_TI2; };
+template <> struct coot_in_code<3> { static constexpr int S = COOT_TI3; };
+
+// VEC elements of every input at (row, j)
+__device__ __forceinline__ void coot_load_vec(const coot_params& p, coot_i64 j, coot_i64 row,
+                                              COOT_REAL (&x)[4][COOT_VEC]) {
+#define COOT_LOAD_ONE(I)                                                                  \
+  if constexpr (I < COOT_NIN) {                                                           \
+    constexpr int S = coot_in_code<I>::S;                                                 \
+    typedef typename coot_st<S>::T T;                                                     \
+    coot_vload<S, COOT_VEC>((const T*)p.in[I] + (j * p.ld_in[I] + row), x[I]);           \
+  } else {                                                                                \
+    _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = (COOT_REAL)0;          \
+  }
+  COOT_LOAD_ONE(0)
+  COOT_LOAD_ONE(1)
+  COOT_LOAD_ONE(2)
+  COOT_LOAD_ONE(3)
+#undef COOT_LOAD_ONE
+}
+
+// one element of every input at (row, j)
+__device__ __forceinline__ void coot_load_one(const coot_params& p, coot_i64 j, coot_i64 row,
+                                              COOT_REAL (&x)[4]) {
+#define COOT_LOAD_S(I)                                                                    \
+  if constexpr (I < COOT_NIN) {                                                           \
+    constexpr int S = coot_in_code<I>::S;                                                 \
+    typedef typename coot_st<S>::T T;                                                     \
+    x[I] = coot_sload<S>((const T*)p.in[I] + (j * p.ld_in[I] + row));                    \
+  } else {                                                                                \
+    x[I] = (COOT_REAL)0;                                                                  \
+  }
+  COOT_LOAD_S(0)
+  COOT_LOAD_S(1)
+  COOT_LOAD_S(2)
+  COOT_LOAD_S(3)
+#undef COOT_LOAD_S
+}
+
+// ---------------------------------------------------------------- arithmetic helpers
+
+// NaN-propagating minimum / maximum
+__device__ __forceinline__ float coot_min(float a, float b) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float coot_max(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ double coot_min(double a, double b) {
+  return (a != a) ? a : ((b != b) ? b : fmin(a, b));
+}
+__device__ __forceinline__ double coot_max(double a, double b) {
+  return (a != a) ? a : ((b != b) ? b : fmax(a, b));
+}
+
+// s + c += x with TwoSum (Knuth): the rounding error of every addition is
+// carried in c, so the pair holds the running sum to about twice the
+// working precision.
+__device__ __forceinline__ void coot_two_sum(COOT_REAL& s, COOT_REAL& c, COOT_REAL x) {
+  const COOT_REAL t = s + x;
+  const COOT_REAL bp = t - s;
+  const COOT_REAL e = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += e;
+}
+
+// the pair as one FP64 value; once the sum is infinite or NaN the
+// compensation carries inf - inf and is dropped
+__device__ __forceinline__ double coot_pair(COOT_REAL s, COOT_REAL c) {
+  const double sd = (double)s;
+  return isfinite(sd) ? sd + (double)c : sd;
+}
+
+__device__ __forceinline__ COOT_REAL coot_sq(COOT_REAL y) {
+  // a separate rounding of the square: the TwoSum that follows relies on it
+  if constexpr (sizeof(COOT_REAL) == 4) {
+    return __fmul_rn(y, y);
+  } else {
+    return __dmul_rn(y, y);
+  }
+}
+
+__device__ __forceinline__ COOT_REAL coot_abs(COOT_REAL y) {
+  if constexpr (sizeof(COOT_REAL) == 4) {
+    return fabsf(y);
+  } else {
+    return fabs(y);
+  }
+}
+
+// ---------------------------------------------------------------- accumulators
+
+#ifndef COOT_HEADS
+#define COOT_HEADS 0
+#endif
+#define COOT_NHEADS (((COOT_HEADS >> 0) & 1) + ((COOT_HEADS >> 1) & 1) + ((COOT_HEADS >> 2) & 1) + \
+                     ((COOT_HEADS >> 3) & 1) + ((COOT_HEADS >> 4) & 1) + ((COOT_HEADS >> 5) & 1) + \
+                     ((COOT_HEADS >> 6) & 1) + ((COOT_HEADS >> 7) & 1))
+
+struct coot_acc {
+  COOT_REAL s, sc;   // sum
+  COOT_REAL q, qc;   // sum of squares
+  COOT_REAL a, ac;   // sum of magnitudes
+  COOT_REAL mn, mx;  // min, max
+  COOT_REAL mna, mxa;  // min, max magnitude
+
+  __device__ __forceinline__ void init() {
+    s = sc = q = qc = a = ac = (COOT_REAL)0;
+    mn = mna = (COOT_REAL)COOT_INF_F;
+    mx = -(COOT_REAL)COOT_INF_F;
+    mxa = (COOT_REAL)0;
+  }
+  __device__ __forceinline__ void add(COOT_REAL y) {
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, y);
+    if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_sq(y));
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_abs(y));
+    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y);
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y);
+    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
+  }
+  // per-head values as FP64, in head-bit order
+  __device__ __forceinline__ void values(double* v) const {
+    int k = 0;
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) v[k++] = coot_pair(s, sc);
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMSQ) != 0) v[k++] = coot_pair(q, qc);
+    if constexpr ((COOT_HEADS & COOT_HEAD_NORM2) != 0) v[k++] = coot_pair(q, qc);
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) v[k++] = coot_pair(a, ac);
+    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) v[k++] = (double)mn;
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) v[k++] = (double)mx;
+    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) v[k++] = (double)mna;
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) v[k++] = (double)mxa;
+    (void)k;
+  }
+};
+
+// combine rule of head number k (in bit order among the set bits)
+__device__ __forceinline__ unsigned coot_head_bit(int k) {
+  unsigned m = COOT_HEADS;
+  for (int i = 0; i < k; ++i) m &= m - 1;
+  return m & (~m + 1);
+}
+
+__device__ __forceinline__ double coot_combine(unsigned bit, double a, double b) {
+  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return coot_min(a, b);
+  if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_MAXABS) return coot_max(a, b);
+  return a + b;
+}
+
+__device__ __forceinline__ double coot_identity(unsigned bit) {
+  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return COOT_INF_D;
+  if (bit == COOT_HEAD_MAX) return -COOT_INF_D;
+  return 0.0;
+}
+
+// FP64 sum of one value per thread across the block (fixed shuffle tree);
+// the result is valid in thread 0.  All threads of the block must call it.
+__device__ __forceinline__ double coot_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // red may still be read from a previous call
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < COOT_WARPS ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+#if COOT_NHEADS > 0
+// Block-level combine of every head, one FP64 partial per block and head,
+// and the last-arriving block's ordered combine into p.res.
+__device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
+  __shared__ double red[COOT_NHEADS][COOT_WARPS];
+  __shared__ int is_last;
+  double v[COOT_NHEADS];
+  acc.values(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < COOT_NHEADS; ++k) {
+    const unsigned bit = coot_head_bit(k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = coot_combine(bit, v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+    if (lane == 0) red[k][warp] = v[k];
+  }
+  __syncthreads();
+  double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < COOT_NHEADS; ++k) {
+      const unsigned bit = coot_head_bit(k);
+      double w = lane < COOT_WARPS ? red[k][lane] : coot_identity(bit);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
+      if (lane == 0) part[(coot_i64)k * gridDim.x + blockIdx.x] = w;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    coot_u32* counter = (coot_u32*)(p.ws + COOT_WS_COUNTER_OFF);
+    is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // the last block: every thread folds a strided subset of the partials in
+  // index order, then the block combines the thread results
+  for (int k = 0; k < COOT_NHEADS; ++k) {
+    const unsigned bit = coot_head_bit(k);
+    double w = coot_identity(bit);
+    for (coot_u32 b = threadIdx.x; b < gridDim.x; b += COOT_BLOCK)
+      w = coot_combine(bit, w, __ldcg(part + (coot_i64)k * gridDim.x + b));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
+    __syncthreads();
+    if (lane == 0) red[0][warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+      w = lane < COOT_WARPS ? red[0][lane] : coot_identity(bit);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
+      if (lane == 0) p.res[k] = (bit == COOT_HEAD_NORM2) ? sqrt(w) : w;
+    }
+  }
+  if (threadIdx.x == 0) *(coot_u32*)(p.ws + COOT_WS_COUNTER_OFF) = 0u;
+}
+#endif
+
+// ================================================================ kind 0/1: evaluation and full reductions
+
+#if COOT_KIND == 0 || COOT_KIND == 1
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+  constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
+  const coot_i64 upc = (p.n_rows + TILE - 1) / TILE;  // tiles per column
+  const coot_i64 units = upc * p.n_cols;
+  typedef typename coot_st<COOT_TO>::T TO;
+  coot_acc acc;
+  acc.init();
+  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
+    const coot_i64 j = u / upc;
+    const coot_i64 r0 = (u - j * upc) * TILE;
+    if (r0 + TILE <= p.n_rows) {
+      COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
+#pragma unroll
+      for (int k = 0; k < COOT_UNROLL; ++k)
+        coot_load_vec(p, j, r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC, xv[k]);
+#pragma unroll
+      for (int k = 0; k < COOT_UNROLL; ++k) {
+        COOT_REAL y[COOT_VEC];
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v) {
+          const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
+          y[v] = coot_f(x);
+          acc.add(y[v]);
+        }
+#if COOT_STORE
+        coot_vstore<COOT_TO, COOT_VEC>(
+            (TO*)p.out + (j * p.ld_out + r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC), y);
+#endif
+      }
+    } else {
+      // the ragged end of a column, one element at a time
+#pragma unroll 1
+      for (int k = 0; k < COOT_UNROLL; ++k) {
+#pragma unroll 1
+        for (int v = 0; v < COOT_VEC; ++v) {
+          const coot_i64 row = r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC + v;
+          if (row < p.n_rows) {
+            COOT_REAL x[4];
+            coot_load_one(p, j, row, x);
+            const COOT_REAL y = coot_f(x);
+            acc.add(y);
+#if COOT_STORE
+            coot_sstore<COOT_TO>((TO*)p.out + (j * p.ld_out + row), y);
+#endif
+          }
+        }
+      }
+    }
+  }
+#if COOT_NHEADS > 0
+  coot_finish_full(acc, p);
+#endif
+}
+#endif
+
+// ================================================================ kind 2: column sums (dim = 0)
+
+#if COOT_KIND == 2
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+  constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
+  __shared__ double red[COOT_WARPS];
+  typedef typename coot_st<COOT_TO>::T TO;
+  const coot_i64 S = p.split;
+  const coot_i64 units = p.n_cols * S;
+  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
+    const coot_i64 j = u / S;
+    const coot_i64 s = u - j * S;
+    const coot_i64 rb = s * p.rows_per_split;
+    const coot_i64 re = min(p.n_rows, rb + p.rows_per_split);
+    COOT_REAL acc = 0, accc = 0;
+    for (coot_i64 r0 = rb; r0 < re; r0 += TILE) {
+      if (r0 + TILE <= re) {
+        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
+#pragma unroll
+        for (int k = 0; k < COOT_UNROLL; ++k)
+          coot_load_vec(p, j, r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC, xv[k]);
+#pragma unroll
+        for (int k = 0; k < COOT_UNROLL; ++k)
+#pragma unroll
+          for (int v = 0; v < COOT_VEC; ++v) {
+            const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
+            coot_two_sum(acc, accc, coot_f(x));
+          }
+      } else {
+#pragma unroll 1
+        for (coot_i64 row = r0 + threadIdx.x; row < re; row += COOT_BLOCK) {
+          COOT_REAL x[4];
+          coot_load_one(p, j, row, x);
+          coot_two_sum(acc, accc, coot_f(x));
+        }
+      }
+    }
+    const double tot = coot_block_sum(coot_pair(acc, accc), red);
+    if (threadIdx.x == 0) {
+      if (S == 1) {
+        ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(tot);
+      } else {
+        double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
+        coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
+        part[j * S + s] = tot;
+        __threadfence();
+        if (atomicAdd(cnt + j, 1u) == (coot_u32)(S - 1)) {
+          __threadfence();
+          double t = 0.0;
+          for (coot_i64 q = 0; q < S; ++q) t += __ldcg(part + j * S + q);
+          ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(t);
+          cnt[j] = 0u;
+        }
+      }
+    }
+  }
+}
+#endif
+
+// ================================================================ kind 3: row sums (dim = 1)
+
+#if COOT_KIND == 3
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+  constexpr coot_i64 PANEL = (coot_i64)COOT_BLOCK * COOT_VEC;  // rows per panel
+  __shared__ int is_last;
+  typedef typename coot_st<COOT_TO>::T TO;
+  const coot_i64 n_panels = (p.n_rows + PANEL - 1) / PANEL;
+  const coot_i64 C = p.split;                               // column chunks
+  const coot_i64 Q = (p.n_cols + C - 1) / C;                // columns per chunk
+  const coot_i64 units = n_panels * C;
+  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
+    const coot_i64 chunk = u / n_panels;
+    const coot_i64 panel = u - chunk * n_panels;
+    const coot_i64 i0 = panel * PANEL + (coot_i64)threadIdx.x * COOT_VEC;
+    const coot_i64 jb = chunk * Q;
+    const coot_i64 je = min(p.n_cols, jb + Q);
+    COOT_REAL s[COOT_VEC], c[COOT_VEC];
+#pragma unroll
+    for (int v = 0; v < COOT_VEC; ++v) s[v] = c[v] = 0;
+    if (panel * PANEL + PANEL <= p.n_rows) {
+      coot_i64 j = jb;
+      for (; j + COOT_UNROLL <= je; j += COOT_UNROLL) {
+        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
+#pragma unroll
+        for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j + k, i0, xv[k]);
+#pragma unroll
+        for (int k = 0; k < COOT_UNROLL; ++k)
+#pragma unroll
+          for (int v = 0; v < COOT_VEC; ++v) {
+            const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
+            coot_two_sum(s[v], c[v], coot_f(x));
+          }
+      }
+      for (; j < je; ++j) {
+        COOT_REAL xv[4][COOT_VEC];
+        coot_load_vec(p, j, i0, xv);
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v) {
+          const COOT_REAL x[4] = {xv[0][v], xv[1][v], xv[2][v], xv[3][v]};
+          coot_two_sum(s[v], c[v], coot_f(x));
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (coot_i64 j = jb; j < je; ++j) {
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v) {
+          if (i0 + v < p.n_rows) {
+            COOT_REAL x[4];
+            coot_load_one(p, j, i0 + v, x);
+            coot_two_sum(s[v], c[v], coot_f(x));
+          }
+        }
+      }
+    }
+    if (C == 1) {
+#pragma unroll
+      for (int v = 0; v < COOT_VEC; ++v)
+        if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(coot_pair(s[v], c[v]));
+    } else {
+      double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
+      coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
+#pragma unroll
+      for (int v = 0; v < COOT_VEC; ++v)
+        if (i0 + v < p.n_rows) part[chunk * p.n_rows + i0 + v] = coot_pair(s[v], c[v]);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) is_last = (atomicAdd(cnt + panel, 1u) == (coot_u32)(C - 1));
+      __syncthreads();
+      if (is_last) {
+        __threadfence();
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v) {
+          if (i0 + v < p.n_rows) {
+            double t = 0.0;
+            for (coot_i64 q = 0; q < C; ++q) t += __ldcg(part + q * p.n_rows + i0 + v);
+            ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(t);
+          }
+        }
+        if (threadIdx.x == 0) cnt[panel] = 0u;
+      }
+      __syncthreads();  // is_last is rewritten by the next unit
+    }
+  }
+}
+#endif

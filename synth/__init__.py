@@ -37,6 +37,8 @@ Expression trees are nested tuples ("sexpr"):
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -70,23 +72,40 @@ def splitmix64(seed: int, start: int, n: int) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
+def _chunked(n: int, fill) -> None:
+    """Run fill(start, count) over chunks of [0, n), in threads (numpy
+    releases the GIL).  Element values depend only on their index, so the
+    split does not change the result."""
+    starts = list(range(0, n, _CHUNK))
+    if len(starts) <= 1:
+        for s in starts:
+            fill(s, min(_CHUNK, n - s))
+        return
+    workers = max(1, min(16, os.cpu_count() or 1, len(starts)))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(lambda s: fill(s, min(_CHUNK, n - s)), starts))
+
+
 def uniform01(seed: int, n: int, start: int = 0) -> np.ndarray:
     """FP64 uniforms in [0, 1) with 53 random bits."""
     out = np.empty(n, dtype=np.float64)
-    for s in range(0, n, _CHUNK):
-        m = min(_CHUNK, n - s)
+
+    def fill(s, m):
         z = splitmix64(seed, start + s, m)
         out[s:s + m] = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    _chunked(n, fill)
     return out
 
 
 def uniform_f32(seed: int, n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """FP32 values lo + (hi - lo) * U, rounded to nearest FP32."""
     out = np.empty(n, dtype=np.float32)
-    for s in range(0, n, _CHUNK):
-        m = min(_CHUNK, n - s)
-        u = uniform01(seed, m, start=s)
+
+    def fill(s, m):
+        z = splitmix64(seed, s, m)
+        u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
         out[s:s + m] = (lo + (hi - lo) * u).astype(np.float32)
+    _chunked(n, fill)
     return out
 
 
@@ -96,8 +115,10 @@ def normal_f64(seed: int, n: int, start: int = 0) -> np.ndarray:
     Uses libm log/cos, so the last bits may differ between platforms; no
     stored expected value depends on these draws.
     """
-    u1 = uniform01(stream_seed(seed, 1), n, start)
-    u2 = uniform01(stream_seed(seed, 2), n, start)
+    z1 = splitmix64(stream_seed(seed, 1), start, n)
+    z2 = splitmix64(stream_seed(seed, 2), start, n)
+    u1 = (z1 >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    u2 = (z2 >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
     return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
 
 
@@ -116,30 +137,33 @@ def lognormal_signed(seed: int, n: int, storage: str, sigma: float = 2.0) -> tup
     "f32" -> np.float32.  Returns (array, number of FP16 redraws).
     """
     out = np.empty(n, dtype={"bf16": np.uint16, "f16": np.float16, "f32": np.float32}[storage])
-    redraws = 0
+    redraws = []
     sign_seed = stream_seed(seed, 3)
-    for s in range(0, n, _CHUNK):
-        m = min(_CHUNK, n - s)
+
+    def fill(s, m):
         mag = np.exp(sigma * normal_f64(seed, m, start=s))
         sgn = np.where((splitmix64(sign_seed, s, m) >> np.uint64(63)) == 1, -1.0, 1.0)
         v = sgn * mag
         if storage == "f16":
-            bad = ~np.isfinite(v.astype(np.float16))
+            with np.errstate(over="ignore"):
+                bad = ~np.isfinite(v.astype(np.float16))
             attempt = 0
             while bad.any():
                 attempt += 1
                 idx = np.nonzero(bad)[0]
-                redraws += idx.size
+                redraws.append(idx.size)
                 rs = stream_seed(seed, 100 + attempt)
                 z = normal_f64(rs, m, start=s)[idx]
                 v[idx] = sgn[idx] * np.exp(sigma * z)
-                bad = ~np.isfinite(v.astype(np.float16))
+                with np.errstate(over="ignore"):
+                    bad = ~np.isfinite(v.astype(np.float16))
             out[s:s + m] = v.astype(np.float16)
         elif storage == "bf16":
             out[s:s + m] = _f32_to_bf16_bits(v.astype(np.float32))
         else:
             out[s:s + m] = v.astype(np.float32)
-    return out, redraws
+    _chunked(n, fill)
+    return out, int(sum(redraws))
 
 
 def loguniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:

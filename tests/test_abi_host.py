@@ -1,0 +1,209 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports
+every function include/coot.h declares, the C tree validator agrees with the
+oracle's independent decoder, the Python serializer agrees with the oracle's
+encoder, every kernel kind compiles with NVRTC for sm_103a, injected
+faults and argument errors come back as status codes."""
+import ctypes
+import os
+import re
+import struct
+
+import pytest
+
+import synth
+from oracle import coot_oracle as O
+import paper_2308_03120_gb300 as coot
+from paper_2308_03120_gb300 import _abi
+from paper_2308_03120_gb300.expr import as_expr, serialize, var, exp, sqrt, log, abs_
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2308_03120_gb300 import build
+    build.build()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "coot.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(coot_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(_abi.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _abi.SIGNATURES, n
+
+
+def test_version_and_status_strings():
+    L = _abi.lib()
+    assert L.coot_version() >= 100
+    assert L.coot_status_string(0) == b"COOT_OK"
+    assert L.coot_status_string(12) == b"COOT_ERR_WORKSPACE"
+
+
+def _hdr(n_nodes, n_inputs=1, compute=0, version=1, magic=b"COOT", r0=0, r1=0):
+    return struct.pack("<4sHHBBHI", magic, version, n_nodes, n_inputs, compute, r0, r1)
+
+
+def _node(op, a=0, b=0, imm=0.0, z0=0, z1=0):
+    return struct.pack("<BBHHHd", op, z0, a, b, z1, imm)
+
+
+MALFORMED = [
+    _hdr(1, magic=b"COOX") + _node(0), _hdr(1, version=2) + _node(0), _hdr(0), _hdr(65) + _node(0) * 65,
+    _hdr(1, n_inputs=0) + _node(0), _hdr(1, n_inputs=5) + _node(0), _hdr(1, compute=1) + _node(0),
+    _hdr(1, r0=1) + _node(0), _hdr(2) + _node(0), _hdr(1) + _node(12), _hdr(1) + _node(0, a=1),
+    _hdr(2) + _node(0) + _node(2, a=1), _hdr(2) + _node(0) + _node(8, a=0, b=2),
+    _hdr(2) + _node(0) + _node(2, a=0, b=1), _hdr(1) + _node(1, a=1, imm=1.0), _hdr(1) + _node(0, z0=1),
+    b"COOT",
+]
+
+
+@pytest.mark.parametrize("raw", MALFORMED)
+def test_validator_rejects_what_the_oracle_rejects(raw):
+    with pytest.raises(O.TreeError):
+        O.decode(raw)
+    with pytest.raises(coot.CootError) as e:
+        coot.coot_tree_check(raw)
+    assert e.value.status_name == "COOT_ERR_BAD_TREE"
+
+
+def _trees():
+    out = [synth.AXPY_2X_3Z, synth.SCHUR_XZ, synth.LEAF0, synth.MAT_EXPR, synth.MAT_CHAIN, synth.BATCH_EXPR]
+    out += [synth.random_tree(77 + s, 2 + s % 11, 1 + s % 4) for s in range(30)]
+    return out
+
+
+@pytest.mark.parametrize("sexpr", _trees())
+def test_serializer_matches_oracle_encoder(sexpr):
+    for compute in ("f32", "f64"):
+        n_in = synth.tree_inputs(sexpr)
+        b = serialize(sexpr, compute=compute, n_inputs=n_in)
+        assert b == O.encode(sexpr, n_inputs=n_in, compute=compute)
+        n, comp, h = coot.coot_tree_check(b)
+        assert n == n_in and comp == {"f32": 0, "f64": 3}[compute]
+        assert O.to_sexpr(O.decode(b)) == O.to_sexpr(O.decode(O.encode(sexpr, n_inputs=n_in, compute=compute)))
+
+
+def test_operator_overloading_builds_the_workload_trees():
+    x, z = var(0), var(1)
+    A, B, C, D = var(0), var(1), var(2), var(3)
+    assert (2 * x + 3 * z).sexpr() == synth.AXPY_2X_3Z
+    assert (x % z).sexpr() == synth.SCHUR_XZ
+    assert ((A % B + 2 * C) / (1 + abs(D))).sexpr() == synth.MAT_EXPR
+    assert (exp(-abs_(A % B + 2 * C)) / sqrt(1 + abs(D))).sexpr() == synth.MAT_CHAIN
+    assert (exp(-abs(A)) % B + 0.5 * C).sexpr() == synth.BATCH_EXPR
+    assert (1 - x).sexpr() == ("sub", ("c", 1.0), ("x", 0))
+    assert (x / 4).sexpr() == ("div", ("x", 0), ("c", 4.0))
+    with pytest.raises(TypeError):
+        x * z
+    assert as_expr(synth.MAT_CHAIN).sexpr() == synth.MAT_CHAIN
+
+
+def test_tree_hash_is_stable_and_content_addressed():
+    a = serialize(synth.MAT_EXPR)
+    b = serialize(synth.MAT_CHAIN)
+    assert coot.coot_tree_check(a)[2] == coot.coot_tree_check(a)[2]
+    assert coot.coot_tree_check(a)[2] != coot.coot_tree_check(b)[2]
+
+
+def test_generated_source_inlines_the_tree():
+    src = coot.coot_tree_source(serialize(synth.MAT_CHAIN), 0)
+    assert "expf(" in src and "sqrtf(" in src and "fabsf(" in src
+    assert "#define COOT_NIN 4" in src
+    src64 = coot.coot_tree_source(serialize(synth.MAT_CHAIN, compute="f64"), 1)
+    assert "exp(" in src64 and "#define COOT_REAL double" in src64
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("dt", [0, 1, 2, 3])
+def test_every_kernel_kind_compiles_for_sm103a(kind, dt):
+    t = serialize(synth.MAT_CHAIN, compute="f64" if dt == 3 else "f32")
+    heads = 0xFF if kind in (0, 1) else 0
+    n = coot.coot_tree_compile(t, kind=kind, in_dtype=dt, out_dtype=dt, heads=heads if kind == 1 else 0)
+    assert n > 1000
+
+
+def test_injected_compile_failure_is_a_status(monkeypatch):
+    monkeypatch.setenv("COOT_FAULT", "nvrtc_fail")
+    with pytest.raises(coot.CootError) as e:
+        coot.coot_tree_compile(serialize(synth.AXPY_2X_3Z))
+    assert e.value.status_name == "COOT_ERR_COMPILE"
+    assert "injected" in str(e.value)
+
+
+def _fake(n_rows, n_cols, ld=None, ptr=1 << 20, dtype=0):
+    return _abi.coot_mat(ptr, dtype, 0, n_rows, n_cols, ld if ld is not None else max(n_rows, 1))
+
+
+def _call(name, *args):
+    L = _abi.lib()
+    return getattr(L, name)(*args), (L.coot_last_error() or b"").decode()
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    t = serialize(synth.AXPY_2X_3Z)
+    ins = (_abi.coot_mat * 2)(_fake(10, 3), _fake(10, 4, ptr=1 << 24))
+    out = _fake(10, 3, ptr=1 << 28)
+    st, msg = _call("coot_expr_eval", t, len(t), ins, 2, ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_SHAPE" and "equal sizes" in msg
+    ins = (_abi.coot_mat * 2)(_fake(10, 3), _fake(10, 3, ptr=1 << 24))
+    st, _ = _call("coot_expr_eval", t, len(t), ins, 1, ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    # partial overlap with input 0 (shifted by one element)
+    bad = _fake(10, 3, ptr=(1 << 20) + 4)
+    st, msg = _call("coot_expr_eval", t, len(t), ins, 2, ctypes.byref(bad), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_ALIAS"
+    # ld < n_rows
+    st, _ = _call("coot_expr_eval", t, len(t), (_abi.coot_mat * 2)(_fake(10, 3, ld=5), _fake(10, 3)), 2,
+                  ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    # unknown dtype
+    st, _ = _call("coot_expr_eval", t, len(t), (_abi.coot_mat * 2)(_fake(10, 3, dtype=9), _fake(10, 3)), 2,
+                  ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_DTYPE"
+
+
+def test_reduction_argument_errors():
+    leaf = serialize(synth.LEAF0)
+    m = (_abi.coot_mat * 1)(_fake(30, 40))
+    res = ctypes.c_void_p(1 << 30)
+    st, msg = _call("coot_norm", leaf, len(leaf), m, 1, 2, res, ctypes.c_void_p(1 << 32), 1 << 22, None)
+    assert _abi.STATUS[st] == "COOT_ERR_UNSUPPORTED" and "spectral" in msg
+    st, _ = _call("coot_norm", leaf, len(leaf), m, 1, 7, res, ctypes.c_void_p(1 << 32), 1 << 22, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    empty = (_abi.coot_mat * 1)(_fake(0, 5))
+    st, _ = _call("coot_minmax", leaf, len(leaf), empty, 1, res, ctypes.c_void_p(1 << 32), 1 << 22, None)
+    assert _abi.STATUS[st] == "COOT_ERR_EMPTY"
+    st, _ = _call("coot_accu", leaf, len(leaf), m, 1, res, None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_WORKSPACE"
+    out = _fake(1, 41, ptr=1 << 28)
+    st, msg = _call("coot_sum_dim", leaf, len(leaf), m, 1, 0, ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_SHAPE"
+    st, _ = _call("coot_sum_dim", leaf, len(leaf), m, 1, 2, ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    a, b = _fake(1, 6), _fake(5, 1, ptr=1 << 24)
+    st, _ = _call("coot_dot", ctypes.byref(a), ctypes.byref(b), res, None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_SHAPE"
+
+
+def test_device_calls_need_init():
+    # valid arguments that reach the kernel cache: refused without coot_init
+    t = serialize(synth.AXPY_2X_3Z)
+    ins = (_abi.coot_mat * 2)(_fake(10, 3), _fake(10, 3, ptr=1 << 24))
+    out = _fake(10, 3, ptr=1 << 28)
+    st, msg = _call("coot_expr_eval", t, len(t), ins, 2, ctypes.byref(out), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_NOT_INIT"
+
+
+def test_workspace_size_grows_with_rows():
+    a = coot.coot_workspace_size(1)
+    b = coot.coot_workspace_size(1 << 20)
+    assert 65536 < a < b
+    assert b >= 64 * (1 << 20) * 8

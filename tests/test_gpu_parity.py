@@ -1,0 +1,364 @@
+"""GPU parity: every entry point of the C ABI against the FP64 oracle on the
+same seeded inputs, at sizes the oracle handles in seconds that span many
+tiles and end in ragged tails, plus the edge cases (empty, one element,
+vector-width +- 1, misaligned pointers, ld > n_rows, 1 x N and N x 1, in-place
+update, storage types).  Tolerances are described in gpu_util."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2308_03120_gb300 as coot
+import synth
+from oracle import coot_oracle as O
+from paper_2308_03120_gb300.expr import serialize
+from tests.gpu_util import (Out, assert_sum_close, check_elementwise, host_mats, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+X0, X1 = synth.X(0), synth.X(1)
+LEAF = serialize(synth.LEAF0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    from paper_2308_03120_gb300 import build
+    build.build()
+    coot.coot_init(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _f32(r, c, ld=None, lo=-1.0, hi=1.0):
+    return ("f32", r, c, ld, lo, hi)
+
+
+# ---------------------------------------------------------------- element-wise evaluation
+
+def _eval_case(sexpr, specs, seed, out_dtype="f32", out_ld=None, offset=0, compute="f32"):
+    ins = host_mats(specs, seed)
+    n_in = synth.tree_inputs(sexpr)
+    tree = serialize(sexpr, compute=compute, n_inputs=n_in)
+    dev = [to_dev(h, offset) for h in ins[:n_in]]
+    r, c = ins[0].n_rows, ins[0].n_cols
+    out = Out(r, c, out_dtype, ld=out_ld, offset=offset)
+    coot.coot_expr_eval(tree, dev, out.mat)
+    torch.cuda.synchronize()
+    out.check()
+    return check_elementwise(tree, ins[:n_in], out.host())
+
+
+def test_axpy_vectors_full_size():
+    """2x + 3z over n = 1,000,000 uniform[-1, 1] FP32 vectors (Task 2's axpy
+    shape)."""
+    n = 1_000_000
+    rep = _eval_case(synth.AXPY_2X_3Z, [_f32(n, 1), _f32(n, 1)], synth.BASE_SEED)
+    assert rep["skipped"] == 0
+
+
+@pytest.mark.parametrize("shape", [(1037, 605), (4096, 3), (3, 4099), (1, 100003), (100003, 1), (4097, 7)])
+def test_matrix_expressions(shape):
+    r, c = shape
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    for e in (synth.MAT_EXPR, synth.MAT_CHAIN):
+        rep = _eval_case(e, specs, 11)
+        assert rep["skipped"] == 0
+
+
+@pytest.mark.parametrize("ld_pad", [1, 4, 13])
+def test_leading_dimension(ld_pad):
+    r, c = 777, 33
+    ld = r + ld_pad
+    specs = [_f32(r, c, ld), _f32(r, c, ld), _f32(r, c, ld), _f32(r, c, ld, 0.0, 2.0)]
+    _eval_case(synth.MAT_EXPR, specs, 21, out_ld=r + 2 * ld_pad)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_misaligned_pointers(offset):
+    n = 4096 * 5 + 3
+    _eval_case(synth.AXPY_2X_3Z, [_f32(n, 1), _f32(n, 1)], 31, offset=offset)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 1023, 1024, 1025, 4095, 4096, 4097, 8191, 8193])
+def test_sizes_around_vector_and_tile_widths(n):
+    _eval_case(synth.MAT_CHAIN, [_f32(n, 1)] * 3 + [_f32(n, 1, lo=0.0, hi=2.0)], 41 + n)
+
+
+def test_empty_is_a_no_op():
+    for r, c in [(0, 5), (5, 0), (0, 0)]:
+        ins = host_mats([_f32(r, c), _f32(r, c)], 3)
+        out = Out(r, c)
+        coot.coot_expr_eval(serialize(synth.AXPY_2X_3Z), [to_dev(h) for h in ins], out.mat)
+        torch.cuda.synchronize()
+        out.check()
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_trees(seed):
+    n_in = 1 + seed % 4
+    e = synth.random_tree(500 + seed, 2 + seed % 11, n_in)
+    r, c = (1 + 97 * seed) % 3001 + 1, 1 + seed % 5
+    specs = [_f32(r, c, lo=-2.0, hi=2.0) for _ in range(n_in)]
+    _eval_case(e, specs, 900 + seed)
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+def test_low_precision_storage(dt):
+    """2x + 3z with BF16 / FP16 inputs and output: FP32 arithmetic, one
+    rounding to the storage type on the store (the paper's fused conversion,
+    Section 7)."""
+    n = (1 << 20) + 3
+    specs = [(dt, n, 1, None, 0, 0), (dt, n, 1, None, 0, 0)]
+    rep = _eval_case(synth.AXPY_2X_3Z, specs, 77, out_dtype=dt)
+    assert rep["exact_frac"] >= 0.999
+
+
+def test_mixed_storage_types():
+    n = 50_001
+    ins = host_mats([("bf16", n, 1, None, 0, 0), ("f16", n, 1, None, 0, 0), _f32(n, 1)], 5)
+    e = ("add", ("mul", X0, X1), synth.X(2))
+    tree = serialize(e)
+    out = Out(n, 1, "f32")
+    coot.coot_expr_eval(tree, [to_dev(h) for h in ins], out.mat)
+    torch.cuda.synchronize()
+    check_elementwise(tree, ins, out.host())
+
+
+def test_fp64_compute():
+    r, c = 513, 9
+    specs = [("f64", r, c, None, -1.0, 1.0)] * 3 + [("f64", r, c, None, 0.0, 2.0)]
+    _eval_case(synth.MAT_CHAIN, specs, 13, out_dtype="f64", compute="f64")
+
+
+def test_in_place_update():
+    """B = B + 3 A, the paper's Task 2 (B += 3 * A): the output is input 1."""
+    n = 300_001
+    ins = host_mats([_f32(n, 1), _f32(n, 1)], 8)
+    tree = serialize(("add", X1, ("mul", synth.C(3.0), X0)))
+    a, b = to_dev(ins[0]), to_dev(ins[1])
+    coot.coot_expr_eval(tree, [a, b], b)
+    torch.cuda.synchronize()
+    got = synth.HostMat(b.buf.cpu().numpy(), "f32", n, 1, n)
+    check_elementwise(tree, ins, got)
+
+
+def test_partial_overlap_is_rejected():
+    n = 1000
+    ins = host_mats([_f32(n, 1), _f32(n, 1)], 9)
+    a = to_dev(ins[0])
+    shifted = coot.Mat(a.buf, n - 1, 1, n - 1, 1)
+    a_short = coot.Mat(a.buf, n - 1, 1, n - 1, 0)
+    with pytest.raises(coot.CootError) as e:
+        coot.coot_expr_eval(serialize(("neg", X0)), [a_short], shifted)
+    assert e.value.status_name == "COOT_ERR_ALIAS"
+
+
+# ---------------------------------------------------------------- full reductions
+
+def _red_inputs(sexpr, specs, seed):
+    ins = host_mats(specs, seed)
+    n_in = synth.tree_inputs(sexpr)
+    return serialize(sexpr, n_inputs=n_in), ins[:n_in], [to_dev(h) for h in ins[:n_in]]
+
+
+def _terms(tree, ins):
+    v, bound, unsafe = O.error_bound(tree, ins)
+    return v.ravel(order="F"), bound.ravel(order="F")
+
+
+@pytest.mark.parametrize("sexpr", [synth.LEAF0, synth.SCHUR_XZ, synth.MAT_EXPR, synth.MAT_CHAIN])
+@pytest.mark.parametrize("shape", [(1_000_000, 1), (1037, 605), (3, 4099)])
+def test_accu_norm_minmax(sexpr, shape):
+    r, c = shape
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(sexpr, specs, 61)
+    t, e = _terms(tree, ins)
+    g = coot.coot_accu(tree, dev).item()
+    assert_sum_close(g, O.accu(tree, ins), t, e, "accu")
+    g = coot.coot_norm(tree, dev, "fro").item()
+    o = O.norm(tree, ins, "fro")
+    sq_err = 2.0 * np.abs(t) * e + e * e
+    tol_sq = 1e-6 * o * o + 6.0 * math.sqrt(float(np.sum(sq_err ** 2)))
+    assert abs(g * g - o * o) <= tol_sq, (g, o)
+    lo, hi = coot.coot_minmax(tree, dev).tolist()
+    olo, ohi = O.minmax(tree, ins)
+    slack = 0.0 if sexpr == synth.LEAF0 else 2.0 * float(np.max(e))
+    assert abs(lo - olo) <= slack and abs(hi - ohi) <= slack, (lo, olo, hi, ohi)
+
+
+def test_vector_norms():
+    n = 123_457
+    tree, ins, dev = _red_inputs(synth.LEAF0, [_f32(n, 1)], 71)
+    for p in (1, 2, "inf", "-inf"):
+        g = coot.coot_norm(tree, dev, p).item()
+        o = O.norm(tree, ins, p)
+        assert abs(g - o) <= 1e-6 * abs(o), (p, g, o)
+    row = coot.Mat(dev[0].buf, 1, n, 1)
+    g = coot.coot_norm(tree, [row], 2).item()
+    assert abs(g - O.norm(tree, ins, 2)) <= 1e-6 * O.norm(tree, ins, 2)
+
+
+def test_dot():
+    n = 1_000_003
+    ins = host_mats([_f32(n, 1), _f32(n, 1)], 81)
+    a, b = (to_dev(h) for h in ins)
+    g = coot.coot_dot(a, b).item()
+    o = O.dot(*ins)
+    prod = O.logical(ins[0]).ravel() * O.logical(ins[1]).ravel()
+    assert_sum_close(g, o, prod, np.abs(prod) * 2.0 ** -24, "dot")
+    # equal counts, different shapes: a row vector against a column vector
+    row = coot.Mat(a.buf, 1, n, 1)
+    assert coot.coot_dot(row, b).item() == g
+
+
+def test_reduction_heads_in_one_pass():
+    r, c = 2049, 301
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(synth.MAT_EXPR, specs, 91)
+    out = Out(r, c)
+    res = coot.coot_expr_reduce(tree, dev, 0xFF, out=out.mat).tolist()
+    torch.cuda.synchronize()
+    out.check()
+    check_elementwise(tree, ins, out.host())
+    t, e = _terms(tree, ins)
+    assert_sum_close(res[0], O.accu(tree, ins), t, e, "sum")
+    o2 = O.norm(tree, ins, "fro")
+    assert abs(res[1] - o2 * o2) <= 1e-5 * o2 * o2
+    assert abs(res[2] - o2) <= 1e-5 * o2
+    assert abs(res[3] - O._fsum(np.abs(t))) <= 1e-5 * O._fsum(np.abs(t))
+    lo, hi = O.minmax(tree, ins)
+    slack = 2.0 * float(np.max(e))
+    assert abs(res[4] - lo) <= slack and abs(res[5] - hi) <= slack
+    assert abs(res[6] - np.min(np.abs(t))) <= slack and abs(res[7] - np.max(np.abs(t))) <= slack
+
+
+def test_empty_reductions():
+    ins = host_mats([_f32(0, 7)], 1)
+    dev = [to_dev(h) for h in ins]
+    assert coot.coot_accu(LEAF, dev).item() == 0.0
+    assert coot.coot_norm(LEAF, dev, "fro").item() == 0.0
+    with pytest.raises(coot.CootError) as e:
+        coot.coot_minmax(LEAF, dev)
+    assert e.value.status_name == "COOT_ERR_EMPTY"
+
+
+def test_nan_and_inf_propagate():
+    v = np.array([1.0, np.inf, 2.0, -3.0], dtype=np.float32)
+    h = synth.as_mat(v, "f32", 4, 1)
+    d = [to_dev(h)]
+    assert coot.coot_accu(LEAF, d).item() == math.inf
+    lo, hi = coot.coot_minmax(LEAF, d).tolist()
+    assert (lo, hi) == (-3.0, math.inf)
+    v[2] = np.nan
+    d = [to_dev(synth.as_mat(v, "f32", 4, 1))]
+    assert math.isnan(coot.coot_accu(LEAF, d).item())
+    lo, hi = coot.coot_minmax(LEAF, d).tolist()
+    assert math.isnan(lo) and math.isnan(hi)
+
+
+def test_closed_forms_on_gpu():
+    n = 1 << 20
+    x = synth.as_mat(np.arange(1, n + 1, dtype=np.float32), "f32", n, 1)
+    d = [to_dev(x)]
+    assert coot.coot_accu(LEAF, d).item() == n * (n + 1) / 2
+    ones = synth.as_mat(np.ones(8192 * 8192 // 16, dtype=np.float32), "f32", 8192 // 4, 8192 // 4)
+    d1 = [to_dev(ones)]
+    assert coot.coot_accu(LEAF, d1).item() == ones.n_elem
+    assert coot.coot_norm(LEAF, d1, "fro").item() == pytest.approx(math.sqrt(ones.n_elem), rel=1e-12)
+
+
+def test_reductions_are_deterministic():
+    r, c = 3001, 257
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(synth.MAT_CHAIN, specs, 5)
+    a = coot.coot_expr_reduce(tree, dev, 0xFF).cpu().numpy()
+    b = coot.coot_expr_reduce(tree, dev, 0xFF).cpu().numpy()
+    assert a.tobytes() == b.tobytes()
+    o1 = Out(1, c)
+    o2 = Out(1, c)
+    coot.coot_sum_dim(tree, dev, 0, o1.mat)
+    coot.coot_sum_dim(tree, dev, 0, o2.mat)
+    o3 = Out(r, 1)
+    o4 = Out(r, 1)
+    coot.coot_sum_dim(tree, dev, 1, o3.mat)
+    coot.coot_sum_dim(tree, dev, 1, o4.mat)
+    torch.cuda.synchronize()
+    assert o1.host().buf.tobytes() == o2.host().buf.tobytes()
+    assert o3.host().buf.tobytes() == o4.host().buf.tobytes()
+
+
+# ---------------------------------------------------------------- sums along a dimension
+
+@pytest.mark.parametrize("shape", [(1037, 605), (8192, 3), (3, 8192), (1, 999), (999, 1), (300_007, 2),
+                                   (17, 20_000), (0, 5), (5, 0)])
+@pytest.mark.parametrize("sexpr", [synth.LEAF0, synth.MAT_EXPR])
+def test_sum_dim(shape, sexpr):
+    r, c = shape
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(sexpr, specs, 101)
+    v, bound, _ = O.error_bound(tree, ins)
+    for dim in (0, 1):
+        out = Out(1, c) if dim == 0 else Out(r, 1)
+        coot.coot_sum_dim(tree, dev, dim, out.mat)
+        torch.cuda.synchronize()
+        out.check()
+        got = O.logical(out.host()).ravel()
+        want = O.sum_dim(tree, ins, dim)
+        assert got.shape == want.shape
+        terms = v if dim == 0 else v.T          # column k of `terms` feeds result k
+        errs = bound if dim == 0 else bound.T
+        s_abs = np.sum(np.abs(terms), axis=0)
+        tol = 1e-6 * np.abs(want) + np.where(np.abs(want) < 1e-3 * s_abs, 1e-9 * s_abs, 0.0)
+        tol += 6.0 * np.sqrt(np.sum(errs * errs, axis=0))
+        tol += np.abs(want) * 2.0 ** -24       # the result is rounded to FP32 once
+        bad = np.abs(got - want) > tol
+        assert not bad.any(), (dim, int(np.argmax(bad)), got[bad][:3], want[bad][:3])
+
+
+def test_sum_dim_fp64_output_and_ld():
+    r, c, ld = 1500, 41, 1509
+    ins = host_mats([_f32(r, c, ld)], 7)
+    dev = [to_dev(ins[0])]
+    for dim in (0, 1):
+        out = Out(1, c, "f64", ld=3) if dim == 0 else Out(r, 1, "f64")
+        coot.coot_sum_dim(LEAF, dev, dim, out.mat)
+        torch.cuda.synchronize()
+        out.check()
+        got = O.logical(out.host()).ravel()
+        want = O.sum_dim(LEAF, ins, dim)
+        assert np.all(np.abs(got - want) <= 1e-6 * np.abs(want) + 1e-12)
+
+
+def test_sum_identities_on_gpu():
+    """accu(sum(A, 0)) == accu(sum(A, 1)) == accu(A) up to rounding."""
+    r, c = 4099, 1031
+    tree, ins, dev = _red_inputs(synth.MAT_EXPR, [_f32(r, c)] * 3 + [_f32(r, c, lo=0.0, hi=2.0)], 3)
+    o0 = Out(1, c, "f64")
+    o1 = Out(r, 1, "f64")
+    coot.coot_sum_dim(tree, dev, 0, o0.mat)
+    coot.coot_sum_dim(tree, dev, 1, o1.mat)
+    a = coot.coot_accu(tree, dev).item()
+    torch.cuda.synchronize()
+    s0 = math.fsum(O.logical(o0.host()).ravel())
+    s1 = math.fsum(O.logical(o1.host()).ravel())
+    t, e = _terms(tree, ins)
+    tol = 2 * 1e-9 * float(np.sum(np.abs(t))) + 1e-6 * abs(a)
+    assert abs(s0 - a) <= tol and abs(s1 - a) <= tol
+
+
+# ---------------------------------------------------------------- unfused baseline
+
+@pytest.mark.parametrize("sexpr", [synth.AXPY_2X_3Z, synth.MAT_EXPR, synth.MAT_CHAIN, synth.LEAF0])
+def test_unfused_baseline_matches(sexpr):
+    r, c = 1037, 605
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    ins = host_mats(specs, 17)
+    n_in = synth.tree_inputs(sexpr)
+    tree = serialize(sexpr, n_inputs=n_in)
+    out = Out(r, c)
+    coot.coot_unfused_eval(tree, [to_dev(h) for h in ins[:n_in]], out.mat)
+    torch.cuda.synchronize()
+    out.check()
+    check_elementwise(tree, ins[:n_in], out.host())
