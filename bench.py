@@ -76,40 +76,95 @@ def inputs_host(seed):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the
-    timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled DURING the timed region by a
+    host thread polling NVML (read-only queries, libnvidia-ml from the
+    driver) about every millisecond, so that even a short timed region gets
+    samples; falls back to `nvidia-smi -lms 200` when NVML cannot be
+    loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, pci_bus_id=None):
         self.gpu = gpu_index
+        self.pci = pci_bus_id
+        self.samples = []
+        self.max_mhz = None
+        self._stop = None
+        self._thread = None
         self.proc = None
 
+    def _nvml(self):
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        ok = False
+        if self.pci:
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(self.pci.encode(), ctypes.byref(h)) == 0
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(self.gpu, ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        return nv, h
+
     def start(self):
+        import ctypes
+        import threading
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            nv, h = self._nvml()
         except Exception:
-            self.proc = None
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.proc = None
+            return
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self._stop = threading.Event()
+
+        def poll():
+            mhz = ctypes.c_uint()
+            rs = ctypes.c_ulonglong()
+            while not self._stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and get_reasons(h, ctypes.byref(rs)) == 0:
+                    self.samples.append((float(mhz.value), int(rs.value)))
+                time.sleep(0.001)
+        self._thread = threading.Thread(target=poll, daemon=True)
+        self._thread.start()
 
     def stop(self):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=2)
+            sm = [s[0] for s in self.samples]
+            reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "nvml"}
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"], "samples": 0}
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
         except Exception:
             self.proc.kill()
             out = ""
-        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 3]
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            try:
+                bits = int(r[2].strip(), 16)
+            except ValueError:
+                continue
+            reasons |= {name for bit, name in self.REASONS.items() if bits & bit}
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------- oracle (CPU) legs
@@ -224,7 +279,11 @@ def run_coot(args):
     for _ in range(max(args.warmup, 3)):
         step()
     barrier()
-    clocks = Clocks(local)
+    props = torch.cuda.get_device_properties(local)
+    pci = None
+    if hasattr(props, "pci_bus_id"):
+        pci = f"{getattr(props, 'pci_domain_id', 0):08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    clocks = Clocks(local, pci)
     clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier()
@@ -249,62 +308,68 @@ def run_coot(args):
     value = world * STEP_BYTES / (ms_step * 1e-3) / 1e9
 
     # unfused baseline of the same step: one kernel per node, temporaries in HBM
-    tmp = torch.empty(8 * N * N * 4, dtype=torch.uint8, device="cuda")
+    ms_unfused = None
+    if not args.no_unfused:
+        tmp = torch.empty(8 * N * N * 4, dtype=torch.uint8, device="cuda")
 
-    def step_unfused():
-        coot.coot_unfused_eval(t_expr, mats, O1, tmp=tmp)
-        coot.coot_accu(leaf, [O1], out_dev=res[0:1], ws=ws)
-        coot.coot_norm(leaf, [O1], "fro", out_dev=res[1:2], ws=ws)
-        coot.coot_minmax(leaf, [O1], out_dev=res[2:4], ws=ws)
-        coot.coot_unfused_eval(t_chain, mats, O2, tmp=tmp)
-        coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws)
-        coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)
+        def step_unfused():
+            coot.coot_unfused_eval(t_expr, mats, O1, tmp=tmp)
+            coot.coot_accu(leaf, [O1], out_dev=res[0:1], ws=ws)
+            coot.coot_norm(leaf, [O1], "fro", out_dev=res[1:2], ws=ws)
+            coot.coot_minmax(leaf, [O1], out_dev=res[2:4], ws=ws)
+            coot.coot_unfused_eval(t_chain, mats, O2, tmp=tmp)
+            coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws)
+            coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)
 
-    for _ in range(3):
-        step_unfused()
-    torch.cuda.synchronize()
-    u0 = torch.cuda.Event(enable_timing=True)
-    u1 = torch.cuda.Event(enable_timing=True)
-    u0.record(stream)
-    for _ in range(args.steps):
-        step_unfused()
-    u1.record(stream)
-    torch.cuda.synchronize()
-    ms_unfused = u0.elapsed_time(u1) / args.steps
+        for _ in range(3):
+            step_unfused()
+        torch.cuda.synchronize()
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for _ in range(args.steps):
+            step_unfused()
+        u1.record(stream)
+        torch.cuda.synchronize()
+        ms_unfused = u0.elapsed_time(u1) / args.steps
+        del tmp
 
     # end to end through the API from pinned host buffers: inputs in, both
     # stored results and every reduction out, every step
-    pinned_in = [torch.from_numpy(h).pin_memory() for h in host]
-    pin_out1 = torch.empty(N * N, dtype=torch.float32).pin_memory()
-    pin_out2 = torch.empty(N * N, dtype=torch.float32).pin_memory()
-    pin_col = torch.empty(N, dtype=torch.float32).pin_memory()
-    pin_row = torch.empty(N, dtype=torch.float32).pin_memory()
-    pin_res = torch.empty(4, dtype=torch.float64).pin_memory()
+    e2e = None
+    if not args.no_e2e:
+        pinned_in = [torch.from_numpy(h).pin_memory() for h in host]
+        pin_out1 = torch.empty(N * N, dtype=torch.float32).pin_memory()
+        pin_out2 = torch.empty(N * N, dtype=torch.float32).pin_memory()
+        pin_col = torch.empty(N, dtype=torch.float32).pin_memory()
+        pin_row = torch.empty(N, dtype=torch.float32).pin_memory()
+        pin_res = torch.empty(4, dtype=torch.float64).pin_memory()
 
-    def step_e2e():
-        for d, h in zip(dev, pinned_in):
-            d.copy_(h, non_blocking=True)
-        step()
-        pin_out1.copy_(out1, non_blocking=True)
-        pin_out2.copy_(out2, non_blocking=True)
-        pin_col.copy_(col, non_blocking=True)
-        pin_row.copy_(row, non_blocking=True)
-        pin_res.copy_(res, non_blocking=True)
+        def step_e2e():
+            for d, h in zip(dev, pinned_in):
+                d.copy_(h, non_blocking=True)
+            step()
+            pin_out1.copy_(out1, non_blocking=True)
+            pin_out2.copy_(out2, non_blocking=True)
+            pin_col.copy_(col, non_blocking=True)
+            pin_row.copy_(row, non_blocking=True)
+            pin_res.copy_(res, non_blocking=True)
 
-    step_e2e()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e_steps = max(2, min(args.steps, 5))
-    barrier()
-    e0.record(stream)
-    for _ in range(e_steps):
         step_e2e()
-    e1.record(stream)
-    barrier()
-    ms_e2e = e0.elapsed_time(e1) / e_steps
-    h2d = 4 * MAT_BYTES
-    d2h = 2 * MAT_BYTES + 2 * N * 4 + 4 * 8
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e_steps = max(2, min(args.steps, 5))
+        barrier()
+        e0.record(stream)
+        for _ in range(e_steps):
+            step_e2e()
+        e1.record(stream)
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / e_steps
+        e2e = {"value": round(world * STEP_BYTES / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": 4 * MAT_BYTES,
+               "d2h_bytes_per_step": 2 * MAT_BYTES + 2 * N * 4 + 4 * 8}
 
     peak, peak_kind = peaks()
     dom = max(names, key=lambda n: statistics.mean(per_call[n]))
@@ -318,26 +383,27 @@ def run_coot(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, nbytes = oracle_sample(seed, args.cpu_cols)
         cpu = {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"8192 x {args.cpu_cols} column block of every matrix, whole step, {dt:.1f} s"}
+               "sample": f"{N} x {args.cpu_cols} column block of every matrix, whole step, {dt:.1f} s"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_rows": N, "n_cols": N, "step_bytes": STEP_BYTES,
-                       "l2": "inputs larger than L2 (1.07 GB of inputs per step), no flush",
+            "config": {"workload": WORKLOAD if N == 8192 else WORKLOAD.replace("8192x8192", f"{N}x{N}"),
+                       "n_rows": N, "n_cols": N, "step_bytes": STEP_BYTES,
+                       "l2": f"inputs larger than L2 ({4 * MAT_BYTES / 1e9:.2f} GB of inputs per step), no flush",
                        "parallelism": f"replicas x{world}"},
             "frac_of_hbm_peak": round(value / world / peak, 4),
-            "unfused": {"ms_per_step": round(ms_unfused, 4),
-                        "value": round(world * STEP_BYTES / (ms_unfused * 1e-3) / 1e9, 1),
-                        "fused_speedup": round(ms_unfused / ms_step, 3)},
+            "unfused": None if ms_unfused is None else {
+                "ms_per_step": round(ms_unfused, 4),
+                "value": round(world * STEP_BYTES / (ms_unfused * 1e-3) / 1e9, 1),
+                "fused_speedup": round(ms_unfused / ms_step, 3)},
             "calls": calls,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": None},
             "cpu_baseline": cpu,
-            "e2e": {"value": round(world * STEP_BYTES / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
-                    "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }
@@ -349,13 +415,20 @@ def run_coot(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="coot", choices=["coot", "reference"])
     ap.add_argument("--ref-cols", type=int, default=256, help="columns in each reference-arm step's sample")
     ap.add_argument("--cpu-cols", type=int, default=1024, help="columns in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=8192, help="matrix order (8192 is the workload; smaller for profiling)")
+    ap.add_argument("--no-unfused", action="store_true", help="skip the unfused-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     args = ap.parse_args()
+    global N, MAT_BYTES, STEP_BYTES
+    N = args.n
+    MAT_BYTES = N * N * ELEM
+    STEP_BYTES = sum(STREAMS.values()) * MAT_BYTES
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -267,6 +267,54 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_ma
                              size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched evaluation: many small matrices of uneven shapes in ONE launch.
+ * The paper notes that small matrices leave most of a GPU idle (Section 3)
+ * and plans a Cube type for collections of matrices (Section 6); here a
+ * persistent kernel walks a work list that covers every matrix, so a batch
+ * costs one launch (and can be replayed as one CUDA-graph node).
+ * ---------------------------------------------------------------------- */
+
+/* One matrix of a batch (device pointers; 8-byte fields).  Every matrix of
+ * a batch shares the tree and the storage types given to the call.  Slots
+ * the tree does not use may be NULL.  `out` (element-wise values, ld_out)
+ * and `colsum` (sum(out, 0): n_cols values, ld_colsum apart) are each
+ * optional (NULL). */
+typedef struct coot_batch_item {
+  const void* in[4];
+  int64_t ld_in[4];
+  void* out;
+  int64_t ld_out;
+  void* colsum;
+  int64_t ld_colsum;
+  int64_t n_rows;
+  int64_t n_cols;
+} coot_batch_item;
+
+/* Size in bytes of the plan (the items plus the work list) for a batch and
+ * the number of work units in it.  Host-only; items is a host array. */
+coot_status coot_batch_plan_size(const coot_batch_item* items, int n_items, size_t* bytes,
+                                 int64_t* n_work);
+
+/* Validate the items for a tree with n_inputs input slots (every used slot
+ * non-NULL, every ld large enough) and write the plan into the HOST buffer
+ * plan_host (plan_bytes from coot_batch_plan_size).  The caller copies it
+ * to device memory once and passes that copy to coot_expr_eval_batched.
+ * Items with n_rows <= 512 are the intended case; any size is accepted. */
+coot_status coot_batch_plan_build(const coot_batch_item* items, int n_items, int n_inputs,
+                                  void* plan_host, size_t plan_bytes);
+
+/* Evaluate tree over every matrix of the plan in one kernel launch: out =
+ * tree(in...) and colsum = sum(out, 0) per matrix.  in_dtypes: host array
+ * of n_inputs storage types; out_dtype: storage type of every out;
+ * colsum_dtype: COOT_F32 or COOT_F64.  plan_dev: the device copy of a plan
+ * built for this batch (the contents are trusted: build it with
+ * coot_batch_plan_build), n_items / n_work as built.  Column sums are
+ * formed in a fixed order (deterministic). */
+coot_status coot_expr_eval_batched(const uint8_t* tree, size_t tree_len, const int32_t* in_dtypes,
+                                   int32_t out_dtype, int32_t colsum_dtype, const void* plan_dev,
+                                   int n_items, int64_t n_work, void* stream);
+
+/* ------------------------------------------------------------------------
  * Unfused baseline: the paper's own evaluation strategy, one kernel launch
  * per operator node with each intermediate result in an HBM temporary
  * (Section 7: every apply() launches at least one kernel; the last node

@@ -30,6 +30,7 @@ __all__ = [
     "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
     "coot_norm", "coot_minmax", "coot_expr_reduce", "coot_unfused_eval", "coot_unfused_tmp_count",
     "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "serialize",
+    "batch_item", "coot_batch_plan", "coot_expr_eval_batched",
 ]
 
 _TORCH_DTYPES = None
@@ -248,3 +249,49 @@ def coot_unfused_eval(tree: bytes, ins, out: Mat, tmp=None, stream=None) -> None
     _abi.call("coot_unfused_eval", tree, len(tree), arr, n, ctypes.byref(o), ctypes.c_void_p(tmp.data_ptr()),
               tmp.numel() * tmp.element_size(), _stream(stream))
     return tmp
+
+
+# ---------------------------------------------------------------- batched evaluation
+
+def batch_item(ins, out: Mat | None = None, colsum: Mat | None = None) -> _abi.coot_batch_item:
+    """One matrix of a batch: inputs (Mats of equal shape), optional
+    element-wise output and optional 1 x n_cols column-sum output."""
+    it = _abi.coot_batch_item()
+    r, c = ins[0].n_rows, ins[0].n_cols
+    for k, m in enumerate(ins):
+        cm = m.c()
+        it.in_[k] = cm.ptr
+        it.ld_in[k] = cm.ld
+    for k in range(len(ins), 4):
+        it.ld_in[k] = max(r, 1)
+    if out is not None:
+        co = out.c()
+        it.out, it.ld_out = co.ptr, co.ld
+    else:
+        it.ld_out = max(r, 1)
+    if colsum is not None:
+        cs = colsum.c()
+        it.colsum, it.ld_colsum = cs.ptr, cs.ld if colsum.n_rows == 1 else 1
+    else:
+        it.ld_colsum = 1
+    it.n_rows, it.n_cols = r, c
+    return it
+
+
+def coot_batch_plan(items, n_inputs: int, device="cuda"):
+    """Build the plan of a batch on the host and copy it to the device once.
+    Returns (plan tensor, n_items, n_work)."""
+    import torch
+    arr = (_abi.coot_batch_item * len(items))(*items)
+    nbytes, n_work = ctypes.c_size_t(), ctypes.c_int64()
+    _abi.call("coot_batch_plan_size", arr, len(items), ctypes.byref(nbytes), ctypes.byref(n_work))
+    host = torch.empty(max(nbytes.value, 16), dtype=torch.uint8)
+    _abi.call("coot_batch_plan_build", arr, len(items), n_inputs, ctypes.c_void_p(host.data_ptr()), nbytes.value)
+    return host.to(device), len(items), n_work.value
+
+
+def coot_expr_eval_batched(tree: bytes, in_dtypes, out_dtype: int, colsum_dtype: int, plan, n_items: int,
+                           n_work: int, stream=None) -> None:
+    dts = (ctypes.c_int32 * 4)(*(list(in_dtypes) + [0] * (4 - len(in_dtypes))))
+    _abi.call("coot_expr_eval_batched", tree, len(tree), dts, out_dtype, colsum_dtype,
+              ctypes.c_void_p(plan.data_ptr()), n_items, n_work, _stream(stream))

@@ -84,3 +84,17 @@ def call(name: str, *args) -> None:
     status = getattr(L, name)(*args)
     if status != 0:
         raise CootError(name, status, (L.coot_last_error() or b"").decode(errors="replace"))
+
+
+class coot_batch_item(ctypes.Structure):
+    _fields_ = [("in_", c_void_p * 4), ("ld_in", c_int64 * 4), ("out", c_void_p), ("ld_out", c_int64),
+                ("colsum", c_void_p), ("ld_colsum", c_int64), ("n_rows", c_int64), ("n_cols", c_int64)]
+
+
+_itemp = POINTER(coot_batch_item)
+SIGNATURES.update({
+    "coot_batch_plan_size": (c_int, [_itemp, c_int, POINTER(c_size_t), POINTER(c_int64)]),
+    "coot_batch_plan_build": (c_int, [_itemp, c_int, c_int, c_void_p, c_size_t]),
+    "coot_expr_eval_batched": (c_int, [_u8p, c_size_t, POINTER(c_int32), c_int32, c_int32, c_void_p, c_int,
+                                       c_int64, c_void_p]),
+})

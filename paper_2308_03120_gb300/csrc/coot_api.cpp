@@ -524,6 +524,101 @@ coot_status coot_sum_dim(const uint8_t* tree, size_t len, const coot_mat* in, in
   return run_sum_dim(t, in, n_in, dim, out, ws, ws_bytes, stream);
 }
 
+// ------------------------------------------------------------ batched evaluation
+
+struct WorkUnit {
+  int32_t item, col0, n_cols, pad;
+};
+static_assert(sizeof(coot_batch_item) == 14 * 8, "coot_batch_item layout");
+static_assert(sizeof(WorkUnit) == 16, "work unit layout");
+
+// columns of one matrix handled by one warp
+static int64_t cols_per_unit(int64_t n_rows) { return n_rows >= 32 ? 1 : (n_rows == 0 ? 32 : 32 / n_rows); }
+
+coot_status coot_batch_plan_size(const coot_batch_item* items, int n_items, size_t* bytes, int64_t* n_work) {
+  clear_error();
+  if ((items == nullptr && n_items > 0) || n_items < 0 || bytes == nullptr)
+    return fail(COOT_ERR_INVALID_ARG, "bad batch");
+  int64_t w = 0;
+  for (int i = 0; i < n_items; ++i) {
+    if (items[i].n_rows < 0 || items[i].n_cols < 0) return fail(COOT_ERR_INVALID_ARG, "negative size in batch");
+    const int64_t k = cols_per_unit(items[i].n_rows);
+    w += (items[i].n_cols + k - 1) / k;
+  }
+  *bytes = sizeof(coot_batch_item) * (size_t)n_items + sizeof(WorkUnit) * (size_t)w;
+  if (n_work) *n_work = w;
+  return COOT_OK;
+}
+
+coot_status coot_batch_plan_build(const coot_batch_item* items, int n_items, int n_inputs, void* plan_host,
+                                  size_t plan_bytes) {
+  clear_error();
+  if (n_inputs < 1 || n_inputs > 4) return fail(COOT_ERR_INVALID_ARG, "n_inputs must be 1..4");
+  size_t need = 0;
+  int64_t n_work = 0;
+  coot_status s = coot_batch_plan_size(items, n_items, &need, &n_work);
+  if (s != COOT_OK) return s;
+  if (plan_host == nullptr || plan_bytes < need) return fail(COOT_ERR_INVALID_ARG, "plan buffer too small");
+  for (int i = 0; i < n_items; ++i) {
+    const coot_batch_item& it = items[i];
+    const std::string at = "batch item " + std::to_string(i) + ": ";
+    if (it.n_rows > INT32_MAX || it.n_cols > INT32_MAX) return fail(COOT_ERR_INVALID_ARG, at + "too large");
+    const bool empty = it.n_rows == 0 || it.n_cols == 0;
+    for (int k = 0; k < n_inputs; ++k) {
+      if (it.in[k] == nullptr && !empty) return fail(COOT_ERR_INVALID_ARG, at + "input " + std::to_string(k) + " is NULL");
+      if (it.ld_in[k] < std::max<int64_t>(it.n_rows, 1)) return fail(COOT_ERR_INVALID_ARG, at + "ld < n_rows");
+    }
+    if (it.out && it.ld_out < std::max<int64_t>(it.n_rows, 1)) return fail(COOT_ERR_INVALID_ARG, at + "ld_out < n_rows");
+    if (it.colsum && it.ld_colsum < 1) return fail(COOT_ERR_INVALID_ARG, at + "ld_colsum < 1");
+  }
+  std::memcpy(plan_host, items, sizeof(coot_batch_item) * (size_t)n_items);
+  WorkUnit* w = reinterpret_cast<WorkUnit*>(static_cast<char*>(plan_host) + sizeof(coot_batch_item) * (size_t)n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const int64_t k = cols_per_unit(items[i].n_rows);
+    for (int64_t c = 0; c < items[i].n_cols; c += k) {
+      *w++ = WorkUnit{i, (int32_t)c, (int32_t)std::min<int64_t>(k, items[i].n_cols - c), 0};
+    }
+  }
+  return COOT_OK;
+}
+
+coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_t* in_dtypes, int32_t out_dtype,
+                                   int32_t colsum_dtype, const void* plan_dev, int n_items, int64_t n_work,
+                                   void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  if (in_dtypes == nullptr) return fail(COOT_ERR_INVALID_ARG, "in_dtypes is NULL");
+  for (int i = 0; i < t.n_inputs; ++i)
+    if (dtype_size(in_dtypes[i]) == 0) return fail(COOT_ERR_DTYPE, "unknown input dtype");
+  if (dtype_size(out_dtype) == 0) return fail(COOT_ERR_DTYPE, "unknown output dtype");
+  if (colsum_dtype != COOT_F32 && colsum_dtype != COOT_F64)
+    return fail(COOT_ERR_DTYPE, "column sums are stored as FP32 or FP64");
+  if (n_items < 0 || n_work < 0) return fail(COOT_ERR_INVALID_ARG, "negative batch size");
+  if (n_work == 0) return COOT_OK;
+  if (plan_dev == nullptr) return fail(COOT_ERR_INVALID_ARG, "plan is NULL");
+  KernelSpec spec;
+  spec.kind = KIND_BATCHED;
+  for (int i = 0; i < t.n_inputs; ++i) spec.in_dtype[i] = in_dtypes[i];
+  spec.out_dtype = out_dtype;
+  spec.store = true;
+  spec.vec = 1;
+  spec.unroll = 4;
+  spec.block = 256;
+  const Compiled* c = nullptr;
+  s = get_kernel(generate_source(t, spec), spec, &c);
+  if (s != COOT_OK) return s;
+  coot_params_host p;
+  std::memset(&p, 0, sizeof p);
+  p.plan = plan_dev;
+  p.split = n_items;
+  p.n_work = n_work;
+  p.rows_per_split = colsum_dtype;
+  const int64_t warps = spec.block / 32;
+  return launch(c, (n_work + warps - 1) / warps, INT32_MAX, spec.block, &p, stream);
+}
+
 coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
   coot_status s = check_mat(a, "a");

@@ -55,6 +55,9 @@ struct KernelSpec {
 // embedded device runtime.
 std::string generate_source(const Tree& t, const KernelSpec& spec);
 
+// Name of the kernel's entry point (one per kind, so profiles tell them apart).
+const char* entry_name(const KernelSpec& spec);
+
 // ------------------------------------------------------------ JIT
 
 // A loaded kernel (cudaKernel_t) plus its static resource use.

@@ -165,7 +165,7 @@ coot_status get_kernel(const std::string& source, const KernelSpec& spec, const 
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
   cudaKernel_t k;
-  e = cudaLibraryGetKernel(&k, lib, "coot_kernel");
+  e = cudaLibraryGetKernel(&k, lib, entry_name(spec));
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
   Compiled c;
   c.kernel = (void*)k;

@@ -140,16 +140,27 @@ static std::string tree_function(const Tree& t) {
   return s;
 }
 
+const char* entry_name(const KernelSpec& spec) {
+  switch (spec.kind) {
+    case KIND_MAP: return spec.heads ? "coot_map_reduce" : "coot_map";
+    case KIND_REDUCE: return "coot_reduce";
+    case KIND_COLSUM: return "coot_colsum";
+    case KIND_ROWSUM: return "coot_rowsum";
+    default: return "coot_batched";
+  }
+}
+
 std::string generate_source(const Tree& t, const KernelSpec& spec) {
   char pre[1024];
   std::snprintf(pre, sizeof pre,
                 "// generated: tree %016" PRIx64 "\n"
+                "#define COOT_ENTRY %s\n"
                 "#define COOT_KIND %d\n#define COOT_NIN %d\n"
                 "#define COOT_TI0 %d\n#define COOT_TI1 %d\n#define COOT_TI2 %d\n#define COOT_TI3 %d\n"
                 "#define COOT_TO %d\n#define COOT_STORE %d\n#define COOT_HEADS %uu\n"
                 "#define COOT_REAL %s\n#define COOT_VEC %d\n#define COOT_UNROLL %d\n"
                 "#define COOT_BLOCK %d\n#define COOT_NC %d\n",
-                t.hash, spec.kind, t.n_inputs, spec.in_dtype[0], spec.in_dtype[1], spec.in_dtype[2],
+                t.hash, entry_name(spec), spec.kind, t.n_inputs, spec.in_dtype[0], spec.in_dtype[1], spec.in_dtype[2],
                 spec.in_dtype[3], spec.out_dtype, spec.store ? 1 : 0, spec.heads,
                 t.compute == COOT_F32 ? "float" : "double", spec.vec, spec.unroll, spec.block,
                 spec.nc ? 1 : 0);

@@ -483,7 +483,7 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
 // ================================================================ kind 0/1: evaluation and full reductions
 
 #if COOT_KIND == 0 || COOT_KIND == 1
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
   constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
   const coot_i64 upc = (p.n_rows + TILE - 1) / TILE;  // tiles per column
   const coot_i64 units = upc * p.n_cols;
@@ -541,7 +541,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __gri
 // ================================================================ kind 2: column sums (dim = 0)
 
 #if COOT_KIND == 2
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
   constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
   __shared__ double red[COOT_WARPS];
   typedef typename coot_st<COOT_TO>::T TO;
@@ -597,10 +597,134 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __gri
 }
 #endif
 
+// ================================================================ kind 4: batched evaluation
+
+// One matrix of a batch (the layout of coot_batch_item in coot.h; every
+// field is 8 bytes).
+struct coot_batch_item_d {
+  const void* in[4];
+  coot_i64 ld_in[4];
+  void* out;
+  coot_i64 ld_out;
+  void* colsum;
+  coot_i64 ld_colsum;
+  coot_i64 n_rows;
+  coot_i64 n_cols;
+};
+
+// One unit of the work list: columns [col0, col0 + n_cols) of one matrix,
+// handled by one warp.  Matrices with at least 32 rows give one column per
+// unit; shorter columns are packed, floor(32 / n_rows) per unit.
+struct coot_work_d {
+  int item;
+  int col0;
+  int n_cols;
+  int pad;
+};
+
+#if COOT_KIND == 4
+__device__ __forceinline__ void coot_load_item(const coot_batch_item_d& it, coot_i64 j, coot_i64 row,
+                                               COOT_REAL (&x)[4]) {
+#define COOT_LOAD_B(I)                                                                    \
+  if constexpr (I < COOT_NIN) {                                                           \
+    constexpr int S = coot_in_code<I>::S;                                                 \
+    typedef typename coot_st<S>::T T;                                                     \
+    x[I] = coot_sload<S>((const T*)it.in[I] + (j * it.ld_in[I] + row));                  \
+  } else {                                                                                \
+    x[I] = (COOT_REAL)0;                                                                  \
+  }
+  COOT_LOAD_B(0)
+  COOT_LOAD_B(1)
+  COOT_LOAD_B(2)
+  COOT_LOAD_B(3)
+#undef COOT_LOAD_B
+}
+
+// p.plan: items (p.split of them) followed by the work list (p.n_work units).
+// COOT_TO is the storage code of the element-wise outputs; the column sums
+// are stored in the storage code given by p.rows_per_split (0 FP32, 3 FP64).
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
+  __shared__ double wbuf[COOT_WARPS][32];
+  typedef typename coot_st<COOT_TO>::T TO;
+  const coot_batch_item_d* items = (const coot_batch_item_d*)p.plan;
+  const coot_work_d* work = (const coot_work_d*)(items + p.split);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const coot_i64 n_warps = (coot_i64)gridDim.x * COOT_WARPS;
+  const bool sum64 = p.rows_per_split == 3;
+  for (coot_i64 w = (coot_i64)blockIdx.x * COOT_WARPS + warp; w < p.n_work; w += n_warps) {
+    const coot_work_d wk = work[w];
+    const coot_batch_item_d it = items[wk.item];
+    const coot_i64 R = it.n_rows;
+    if (R >= 32) {
+      const coot_i64 j = wk.col0;
+      COOT_REAL s = 0, c = 0;
+      for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
+        COOT_REAL xv[COOT_UNROLL][4];
+#pragma unroll
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 r = r0 + 32 * q + lane;
+          if (r < R) coot_load_item(it, j, r, xv[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 r = r0 + 32 * q + lane;
+          if (r < R) {
+            const COOT_REAL y = coot_f(xv[q]);
+            if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
+            coot_two_sum(s, c, y);
+          }
+        }
+      }
+      if (it.colsum) {
+        double v = coot_pair(s, c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+          if (sum64) {
+            ((double*)it.colsum)[j * it.ld_colsum] = v;
+          } else {
+            ((float*)it.colsum)[j * it.ld_colsum] = (float)v;
+          }
+        }
+      }
+    } else {
+      // wk.n_cols short columns side by side: lane -> (column, row)
+      const int k = wk.n_cols;
+      const int Ri = (int)R;
+      double y64 = 0.0;
+      if (lane < k * Ri) {
+        const int cl = lane / Ri, r = lane - cl * Ri;
+        const coot_i64 j = wk.col0 + cl;
+        COOT_REAL x[4];
+        coot_load_item(it, j, r, x);
+        const COOT_REAL y = coot_f(x);
+        if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
+        y64 = (double)y;
+      }
+      if (it.colsum) {
+        wbuf[warp][lane] = y64;
+        __syncwarp();
+        if (lane < k) {
+          double t = 0.0;
+          for (int r = 0; r < Ri; ++r) t += wbuf[warp][lane * Ri + r];
+          const coot_i64 j = wk.col0 + lane;
+          if (sum64) {
+            ((double*)it.colsum)[j * it.ld_colsum] = t;
+          } else {
+            ((float*)it.colsum)[j * it.ld_colsum] = (float)t;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+#endif
+
 // ================================================================ kind 3: row sums (dim = 1)
 
 #if COOT_KIND == 3
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) coot_kernel(const __grid_constant__ coot_params p) {
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
   constexpr coot_i64 PANEL = (coot_i64)COOT_BLOCK * COOT_VEC;  // rows per panel
   __shared__ int is_last;
   typedef typename coot_st<COOT_TO>::T TO;

@@ -198,9 +198,9 @@ def as_mat(flat: np.ndarray, dtype: str, n_rows: int, n_cols: int, ld: int | Non
     """Lay a flat column-major array out with leading dimension ld >= n_rows.
     Padding rows (ld > n_rows) hold `pad_value` (NaN by default for float
     types) so that any read of them shows up in a result."""
-    ld = n_rows if ld is None else ld
-    assert ld >= n_rows
-    if ld == n_rows:
+    ld = max(n_rows, 1) if ld is None else ld
+    assert ld >= max(n_rows, 1)
+    if ld == n_rows or (n_cols <= 1 and n_rows > 0):
         return HostMat(np.ascontiguousarray(flat), dtype, n_rows, n_cols, ld)
     buf = np.empty(max(ld * n_cols, 0), dtype=flat.dtype)
     if pad_value is None:

@@ -82,7 +82,7 @@ class Out:
         es = self.t.element_size()
         assert np.all(raw[:self.lo * es] == 0x7F), "guard band before the output was written"
         assert np.all(raw[(self.lo + self.size) * es:] == 0x7F), "guard band after the output was written"
-        if self.ld > self.n_rows and self.n_cols:
+        if self.ld > self.n_rows and self.n_cols and self.size:
             body = raw[self.lo * es:(self.lo + self.size) * es].reshape(self.n_cols, self.ld * es)
             assert np.all(body[:, self.n_rows * es:] == 0x7F), "padding rows were written"
 
