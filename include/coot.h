@@ -315,6 +315,32 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t tree_len, const i
                                    int n_items, int64_t n_work, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Row sums without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory where
+ * they need the reduction (memory reserved up front by an allocator they do
+ * not control, paths that must not synchronise the device the way
+ * cudaMalloc / cudaFree can, C callers without a CUDA allocator).  Its
+ * scratch is a fixed array of about 4 MiB inside the library's device
+ * image, held by every GPU that loads the library until the process exits.
+ * ---------------------------------------------------------------------- */
+
+/* Largest row count coot_sum_rows_f32_static accepts (the scratch holds 16
+ * FP64 partial sums per row). */
+#define COOT_STATIC_MAX_ROWS 32768
+
+/* out = sum(a, 1), the sum of each row (Table 6), for an FP32 matrix a
+ * (n_rows x n_cols, ld) into an FP32 n_rows x 1 out; allocates nothing.
+ * n_rows > COOT_STATIC_MAX_ROWS returns COOT_ERR_UNSUPPORTED.  The first
+ * call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) for that device, with that device current; make
+ * that first call before any stream capture.  Each call clears the
+ * scratch's counters on `stream` (cudaMemsetAsync) before its kernel.
+ * Every call shares the one scratch array: two calls that can run at the
+ * same time on the GPU (different streams, or graph branches without an
+ * ordering between them) race and give wrong sums. */
+coot_status coot_sum_rows_f32_static(const coot_mat* a, const coot_mat* out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Unfused baseline: the paper's own evaluation strategy, one kernel launch
  * per operator node with each intermediate result in an HBM temporary
  * (Section 7: every apply() launches at least one kernel; the last node

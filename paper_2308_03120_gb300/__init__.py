@@ -295,3 +295,10 @@ def coot_expr_eval_batched(tree: bytes, in_dtypes, out_dtype: int, colsum_dtype:
     dts = (ctypes.c_int32 * 4)(*(list(in_dtypes) + [0] * (4 - len(in_dtypes))))
     _abi.call("coot_expr_eval_batched", tree, len(tree), dts, out_dtype, colsum_dtype,
               ctypes.c_void_p(plan.data_ptr()), n_items, n_work, _stream(stream))
+
+
+def coot_sum_rows_f32_static(a: Mat, out: Mat, stream=None) -> None:
+    """sum(a, 1) of an FP32 matrix with the library's own scratch (no
+    workspace, no allocation); n_rows <= 32768."""
+    ca, co = a.c(), out.c()
+    _abi.call("coot_sum_rows_f32_static", ctypes.byref(ca), ctypes.byref(co), _stream(stream))

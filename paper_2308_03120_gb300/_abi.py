@@ -98,3 +98,5 @@ SIGNATURES.update({
     "coot_expr_eval_batched": (c_int, [_u8p, c_size_t, POINTER(c_int32), c_int32, c_int32, c_void_p, c_int,
                                        c_int64, c_void_p]),
 })
+
+SIGNATURES["coot_sum_rows_f32_static"] = (c_int, [_matp, _matp, c_void_p])

@@ -27,7 +27,7 @@ LIB = os.path.join(PKG, "libcoot.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 HOST_SOURCES = ["coot_api.cpp", "coot_tree.cpp", "coot_jit.cpp"]
-CUDA_SOURCES = ["coot_aot.cu"]
+CUDA_SOURCES = ["coot_aot.cu", "coot_static.cu"]
 
 
 def cuda_home() -> str:
