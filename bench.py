@@ -412,6 +412,187 @@ def run_coot(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- other workloads (one JSON line each)
+
+def _timed(torch, stream, fn, steps, warmup):
+    """Device time of `fn` per call (CUDA events on `stream`)."""
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _graph(torch, fn):
+    """`fn` captured once as a CUDA graph (compiled kernels are warmed first)."""
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+    torch.cuda.synchronize()
+    return g
+
+
+def run_vectors(args):
+    """FP32 vectors n = 1,000,000: y = 2x + 3z, accu(x % z), norm2(x).  The
+    step is latency-bound (24 MB fits in L2): reported as microseconds per
+    step, eager calls and as one CUDA graph."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    n = 1_000_000
+    seed = synth.BASE_SEED
+    x = torch.from_numpy(synth.uniform_f32(seed, n)).cuda()
+    z = torch.from_numpy(synth.uniform_f32(seed + 1, n)).cuda()
+    y = torch.empty(n, device="cuda")
+    X, Z, Y = coot.Mat(x, n, 1, n), coot.Mat(z, n, 1, n), coot.Mat(y, n, 1, n)
+    res = torch.empty(2, dtype=torch.float64, device="cuda")
+    ws = coot.Workspace(1)
+    t_axpy = coot.serialize(synth.AXPY_2X_3Z)
+    t_schur = coot.serialize(synth.SCHUR_XZ)
+    leaf = coot.serialize(synth.LEAF0)
+
+    def step(s=None):
+        coot.coot_expr_eval(t_axpy, [X, Z], Y, stream=s)
+        coot.coot_accu(t_schur, [X, Z], out_dev=res[0:1], ws=ws, stream=s)
+        coot.coot_norm(leaf, [X], 2, out_dev=res[1:2], ws=ws, stream=s)
+
+    stream = torch.cuda.current_stream()
+    ms = _timed(torch, stream, step, args.steps, args.warmup)
+    g = _graph(torch, step)
+    ms_g = _timed(torch, stream, g.replay, args.steps, args.warmup)
+    nbytes = (3 + 2 + 1) * n * 4
+    print(json.dumps({"metric": "fused vector step latency", "workload": "vectors n=1e6 fp32: 2x+3z, accu(x%z), "
+                      "norm2(x)", "us_per_step": round(ms * 1e3, 2), "us_per_step_graph": round(ms_g * 1e3, 2),
+                      "gbs_graph": round(nbytes / (ms_g * 1e-3) / 1e9, 1), "bytes_per_step": nbytes,
+                      "launches_per_step": 3, "note": "24 MB per step is L2-resident: latency, not HBM, bound"}))
+
+
+def run_precision(args, dt):
+    """n = 2^28 stored as BF16 or FP16 (signed lognormal, sigma 2): y = 2x + 3z
+    stored in the same type, accu(x) and norm2(x) in one pass, dot(x, z)."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    n = 1 << 28
+    seed = synth.BASE_SEED + 2
+    tdt = torch.bfloat16 if dt == "bf16" else torch.float16
+    hx, _ = synth.lognormal_signed(seed, n, dt)
+    hz, _ = synth.lognormal_signed(seed + 1, n, dt)
+
+    def dev(h):
+        t = torch.from_numpy(h.view(np.int16)).view(tdt) if dt == "bf16" else torch.from_numpy(h)
+        return t.cuda()
+    x, z = dev(hx), dev(hz)
+    y = torch.empty(n, dtype=tdt, device="cuda")
+    X, Z, Y = coot.Mat(x, n, 1, n), coot.Mat(z, n, 1, n), coot.Mat(y, n, 1, n)
+    res = torch.empty(3, dtype=torch.float64, device="cuda")
+    ws = coot.Workspace(1)
+    t_axpy = coot.serialize(synth.AXPY_2X_3Z)
+    leaf = coot.serialize(synth.LEAF0)
+    stream = torch.cuda.current_stream()
+    calls = {
+        "expr_eval 2x+3z": (lambda: coot.coot_expr_eval(t_axpy, [X, Z], Y), 3 * n * 2),
+        "expr_reduce accu+norm2(x)": (lambda: coot.coot_expr_reduce(leaf, [X], coot.HEAD_SUM | coot.HEAD_NORM2,
+                                                                    out_dev=res[0:2], ws=ws), n * 2),
+        "dot(x, z)": (lambda: coot.coot_dot(X, Z, out_dev=res[2:3], ws=ws), 2 * n * 2),
+    }
+    peak, kind = peaks()
+    out = {}
+    total_ms = 0.0
+    total_b = 0
+    for name, (fn, nbytes) in calls.items():
+        ms = _timed(torch, stream, fn, args.steps, args.warmup)
+        out[name] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+        total_ms += ms
+        total_b += nbytes
+    print(json.dumps({"metric": "fused low-precision step HBM GB/s", "workload": f"vectors n=2^28 {dt}",
+                      "value": round(total_b / (total_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                      "frac_of_hbm_peak": round(total_b / (total_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": kind,
+                      "calls": out}))
+
+
+def run_batched(args):
+    """4096 FP32 matrices, rows and cols log-uniform in [1, 512]:
+    out = exp(-abs(A)) % B + 0.5 C and sum(out, 0) per matrix, in one
+    persistent launch captured as a CUDA graph, against one launch per
+    matrix (eager, and the same launches captured as one graph)."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    nmat = 4096
+    rows = synth.loguniform_int(synth.BASE_SEED + 3, nmat, 1, 512)
+    cols = synth.loguniform_int(synth.BASE_SEED + 4, nmat, 1, 512)
+    sizes = (rows * cols).astype(np.int64)
+    # every operand of every matrix packed in one buffer per operand, each
+    # matrix starting on a 16-byte boundary
+    offs = np.zeros(nmat + 1, dtype=np.int64)
+    offs[1:] = np.cumsum((sizes + 3) // 4 * 4)
+    coff = np.zeros(nmat + 1, dtype=np.int64)
+    coff[1:] = np.cumsum((cols + 3) // 4 * 4)
+    total = int(offs[-1])
+    bufs = [torch.from_numpy(synth.uniform_f32(synth.BASE_SEED + 10 + k, total)).cuda() for k in range(3)]
+    out = torch.empty(total, device="cuda")
+    csum = torch.empty(int(coff[-1]), device="cuda")
+    tree = coot.serialize(synth.BATCH_EXPR)
+    items, per = [], []
+    for m in range(nmat):
+        r, c, o = int(rows[m]), int(cols[m]), int(offs[m])
+        ins = [coot.Mat(b, r, c, r, o) for b in bufs]
+        om = coot.Mat(out, r, c, r, o)
+        cm = coot.Mat(csum, 1, c, 1, int(coff[m]))
+        items.append(coot.batch_item(ins, om, cm))
+        per.append((ins, om, cm))
+    plan, n_items, n_work = coot.coot_batch_plan(items, 3)
+    stream = torch.cuda.current_stream()
+
+    def batched(s=None):
+        coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work, stream=s)
+
+    g = _graph(torch, batched)
+    ms_graph = _timed(torch, stream, g.replay, args.steps, args.warmup)
+    ms_eager = _timed(torch, stream, batched, args.steps, args.warmup)
+    ws = coot.Workspace(1)
+
+    def per_matrix(s=None):
+        for ins, om, cm in per:
+            coot.coot_expr_eval(tree, ins, om, stream=s)
+            coot.coot_sum_dim(tree, ins, 0, cm, ws=ws, stream=s)
+
+    ms_per = _timed(torch, stream, per_matrix, max(2, args.steps // 10), 1)
+    gp = _graph(torch, per_matrix)
+    ms_per_graph = _timed(torch, stream, gp.replay, max(2, args.steps // 10), 1)
+    elems = int(sizes.sum())
+    nbytes = elems * 4 * 4 + int(cols.sum()) * 4
+    peak, kind = peaks()
+    print(json.dumps({
+        "metric": "batch evals/s", "workload": "4096 fp32 matrices, rows/cols log-uniform [1,512]: "
+        "exp(-abs(A))%B+0.5C and column sums", "unit": "matrices/s",
+        "value": round(nmat / (ms_graph * 1e-3), 1), "batches_per_s": round(1.0 / (ms_graph * 1e-3), 1),
+        "ms_per_batch_graph": round(ms_graph, 4), "ms_per_batch_eager": round(ms_eager, 4),
+        "gbs": round(nbytes / (ms_graph * 1e-3) / 1e9, 1), "frac_of_hbm_peak": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
+        "elements": elems, "work_units": n_work,
+        "per_matrix_launches": {"ms_eager": round(ms_per, 3), "ms_graph": round(ms_per_graph, 3), "launches": 2 * nmat},
+        "speedup_vs_per_matrix_eager": round(ms_per / ms_graph, 1),
+        "speedup_vs_per_matrix_graph": round(ms_per_graph / ms_graph, 1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,6 +605,9 @@ def main():
     ap.add_argument("--n", type=int, default=8192, help="matrix order (8192 is the workload; smaller for profiling)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--workload", default="matrices",
+                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched"],
+                    help="matrices is the headline line; the others print their own line")
     args = ap.parse_args()
     global N, MAT_BYTES, STEP_BYTES
     N = args.n
@@ -431,6 +615,12 @@ def main():
     STEP_BYTES = sum(STREAMS.values()) * MAT_BYTES
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "vectors":
+        run_vectors(args)
+    elif args.workload in ("precision-bf16", "precision-f16"):
+        run_precision(args, args.workload.split("-")[1])
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_coot(args)
 

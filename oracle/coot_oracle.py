@@ -38,6 +38,7 @@ FP64 value and of the final sum.
 """
 from __future__ import annotations
 
+import itertools
 import math
 import struct
 from dataclasses import dataclass
@@ -456,14 +457,21 @@ def error_bound(tree, mats):
 # Reductions (Table 5, Table 6)
 # --------------------------------------------------------------------------
 
-def _fsum(x: np.ndarray) -> float:
-    x = np.asarray(x, dtype=np.float64).ravel()
-    if x.size == 0:
+def _fsum(x) -> float:
+    """Correctly rounded sum of FP64 values: one math.fsum over every value
+    (an array, or an iterable of arrays fed one after the other), so the
+    values stream through a single exact summation without materialising a
+    Python list of all of them."""
+    parts = [np.asarray(x, dtype=np.float64).ravel()] if isinstance(x, np.ndarray) else \
+        [np.asarray(p, dtype=np.float64).ravel() for p in x]
+    if sum(p.size for p in parts) == 0:
         return 0.0
-    if not np.all(np.isfinite(x)):
+    if not all(np.all(np.isfinite(p)) for p in parts):
         # fsum raises on inf - inf; IEEE summation gives NaN there
-        return float(np.sum(x))
-    return math.fsum(x.tolist())
+        return float(sum(np.sum(p) for p in parts))
+    step = 1 << 20
+    return math.fsum(itertools.chain.from_iterable(p[i:i + step].tolist() for p in parts
+                                                   for i in range(0, p.size, step)))
 
 
 def accu(tree, mats) -> float:

@@ -167,7 +167,7 @@ static Launch heuristic(int kind, int n_in, const View& v) {
   l.vec = pick_vec(v);
   l.block = 256;
   if (kind == KIND_ROWSUM) {
-    l.unroll = n_in >= 3 ? 2 : 4;
+    l.unroll = n_in >= 3 ? 4 : 8;
   } else {
     l.unroll = std::max(1, std::min(4, 8 / std::max(1, n_in)));
   }
@@ -316,30 +316,35 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   p.ws = (unsigned char*)ws;
   const int64_t resident = (int64_t)d.sm_count * std::max(1, c->max_blocks_per_sm);
   const size_t part_bytes = ws ? (ws_bytes > COOT_WS_PARTIALS_OFF ? ws_bytes - COOT_WS_PARTIALS_OFF : 0) : 0;
-  int64_t units;
+  int64_t units;  // blocks' worth of work
   if (dim == 0) {
-    // split tall columns over several blocks when there are too few columns
-    const int64_t tile = tile_rows(l);
+    // a warp per (column, segment); split the columns into segments until
+    // there are about three units per resident warp
+    const int64_t warps = l.block / 32;
+    const int64_t wt = 32LL * l.vec * l.unroll;  // rows per warp tile
+    const int64_t target = 3 * resident * warps;
     int64_t S = 1;
-    if (Cn < resident && R > 4 * tile) {
-      S = std::min<int64_t>((resident + Cn - 1) / Cn, (R + tile - 1) / tile);
-      S = std::min<int64_t>(S, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(Cn, 1))) / 1);
-      if (Cn > COOT_WS_MAX_COUNTERS) S = 1;
+    if (Cn < target && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
+      S = std::min<int64_t>((target + Cn - 1) / Cn, (R + wt - 1) / wt);
+      S = std::min<int64_t>(S, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(Cn, 1))));
       S = std::max<int64_t>(S, 1);
     }
     int64_t rps = (R + S - 1) / S;
-    rps = ((rps + tile - 1) / tile) * tile;
-    if (S > 1) S = (R + rps - 1) / rps;
+    rps = std::max<int64_t>(((rps + wt - 1) / wt) * wt, wt);
+    if (S > 1) S = std::max<int64_t>((R + rps - 1) / rps, 1);
     p.split = S;
-    p.rows_per_split = std::max<int64_t>(rps, 1);
-    units = Cn * S;
+    p.rows_per_split = rps;
+    units = (Cn * S + warps - 1) / warps;
   } else {
-    const int64_t panel = (int64_t)l.block * l.vec;
+    // panels of 64 * vec rows; chunks of columns until about two blocks
+    // per resident block slot
+    const int64_t groups = std::max(1, l.block / 64);
+    const int64_t panel = 64LL * l.vec;
     const int64_t n_panels = (R + panel - 1) / panel;
     int64_t C = std::max<int64_t>(1, (2 * resident + n_panels - 1) / n_panels);
-    C = std::min<int64_t>(C, std::max<int64_t>(Cn, 1));
+    C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));
     C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);
-    C = std::min<int64_t>(C, (int64_t)(part_bytes / (sizeof(double) * R)));
+    C = std::min<int64_t>(C, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(R, 1))));
     if (n_panels > COOT_WS_MAX_COUNTERS) C = 1;
     C = std::max<int64_t>(C, 1);
     p.split = C;

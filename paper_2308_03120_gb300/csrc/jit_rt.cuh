@@ -540,49 +540,54 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
 
 // ================================================================ kind 2: column sums (dim = 0)
 
+// One warp per unit u = (column j, segment s): rows [s R, min((s + 1) R,
+// n_rows)) of column j with R = p.rows_per_split (a multiple of the warp
+// tile), p.split segments per column.  No block-level barrier is needed;
+// with several segments per column the segment sums go to the workspace and
+// the last warp of a column to arrive adds them in segment order.
 #if COOT_KIND == 2
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
-  __shared__ double red[COOT_WARPS];
+  constexpr coot_i64 WT = (coot_i64)32 * COOT_VEC * COOT_UNROLL;  // rows per warp tile
   typedef typename coot_st<COOT_TO>::T TO;
+  const int lane = threadIdx.x & 31;
   const coot_i64 S = p.split;
   const coot_i64 units = p.n_cols * S;
-  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
+  const coot_i64 n_warps = (coot_i64)gridDim.x * COOT_WARPS;
+  for (coot_i64 u = (coot_i64)blockIdx.x * COOT_WARPS + (threadIdx.x >> 5); u < units; u += n_warps) {
     const coot_i64 j = u / S;
     const coot_i64 s = u - j * S;
     const coot_i64 rb = s * p.rows_per_split;
     const coot_i64 re = min(p.n_rows, rb + p.rows_per_split);
     COOT_REAL acc = 0, accc = 0;
-    for (coot_i64 r0 = rb; r0 < re; r0 += TILE) {
-      if (r0 + TILE <= re) {
-        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
+    coot_i64 r0 = rb;
+    for (; r0 + WT <= re; r0 += WT) {
+      COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
 #pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k)
-          coot_load_vec(p, j, r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC, xv[k]);
+      for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j, r0 + ((coot_i64)k * 32 + lane) * COOT_VEC, xv[k]);
 #pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k)
+      for (int k = 0; k < COOT_UNROLL; ++k)
 #pragma unroll
-          for (int v = 0; v < COOT_VEC; ++v) {
-            const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
-            coot_two_sum(acc, accc, coot_f(x));
-          }
-      } else {
-#pragma unroll 1
-        for (coot_i64 row = r0 + threadIdx.x; row < re; row += COOT_BLOCK) {
-          COOT_REAL x[4];
-          coot_load_one(p, j, row, x);
+        for (int v = 0; v < COOT_VEC; ++v) {
+          const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
           coot_two_sum(acc, accc, coot_f(x));
         }
-      }
     }
-    const double tot = coot_block_sum(coot_pair(acc, accc), red);
-    if (threadIdx.x == 0) {
+#pragma unroll 1
+    for (coot_i64 row = r0 + lane; row < re; row += 32) {
+      COOT_REAL x[4];
+      coot_load_one(p, j, row, x);
+      coot_two_sum(acc, accc, coot_f(x));
+    }
+    double v = coot_pair(acc, accc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) {
       if (S == 1) {
-        ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(tot);
+        ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(v);
       } else {
         double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
         coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
-        part[j * S + s] = tot;
+        part[j * S + s] = v;
         __threadfence();
         if (atomicAdd(cnt + j, 1u) == (coot_u32)(S - 1)) {
           __threadfence();
@@ -723,30 +728,41 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
 
 // ================================================================ kind 3: row sums (dim = 1)
 
+// A block is COOT_RT row threads x (COOT_BLOCK / COOT_RT) column groups and
+// owns a panel of COOT_RT * COOT_VEC rows over one chunk of columns; column
+// group g takes the chunk's columns g, g + CG, ... with COOT_UNROLL of them
+// in flight.  The groups are added in shared memory in group order; with
+// several chunks the chunk sums go to the workspace and the last block of a
+// panel to arrive adds them (each group a strided subset of the chunks,
+// then the groups in order), so the order is fixed.
 #if COOT_KIND == 3
+#define COOT_RT 64
+#define COOT_CG (COOT_BLOCK / COOT_RT)
+#define COOT_PANEL (COOT_RT * COOT_VEC)
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  constexpr coot_i64 PANEL = (coot_i64)COOT_BLOCK * COOT_VEC;  // rows per panel
+  __shared__ double red[COOT_CG][COOT_PANEL];
   __shared__ int is_last;
   typedef typename coot_st<COOT_TO>::T TO;
-  const coot_i64 n_panels = (p.n_rows + PANEL - 1) / PANEL;
+  const int tx = threadIdx.x % COOT_RT, ty = threadIdx.x / COOT_RT;
+  const coot_i64 n_panels = (p.n_rows + COOT_PANEL - 1) / COOT_PANEL;
   const coot_i64 C = p.split;                               // column chunks
   const coot_i64 Q = (p.n_cols + C - 1) / C;                // columns per chunk
   const coot_i64 units = n_panels * C;
   for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
     const coot_i64 chunk = u / n_panels;
     const coot_i64 panel = u - chunk * n_panels;
-    const coot_i64 i0 = panel * PANEL + (coot_i64)threadIdx.x * COOT_VEC;
+    const coot_i64 i0 = panel * COOT_PANEL + (coot_i64)tx * COOT_VEC;
     const coot_i64 jb = chunk * Q;
     const coot_i64 je = min(p.n_cols, jb + Q);
     COOT_REAL s[COOT_VEC], c[COOT_VEC];
 #pragma unroll
     for (int v = 0; v < COOT_VEC; ++v) s[v] = c[v] = 0;
-    if (panel * PANEL + PANEL <= p.n_rows) {
-      coot_i64 j = jb;
-      for (; j + COOT_UNROLL <= je; j += COOT_UNROLL) {
+    if (panel * COOT_PANEL + COOT_PANEL <= p.n_rows) {
+      coot_i64 j = jb + ty;
+      for (; j + (coot_i64)(COOT_UNROLL - 1) * COOT_CG < je; j += (coot_i64)COOT_UNROLL * COOT_CG) {
         COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
 #pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j + k, i0, xv[k]);
+        for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j + (coot_i64)k * COOT_CG, i0, xv[k]);
 #pragma unroll
         for (int k = 0; k < COOT_UNROLL; ++k)
 #pragma unroll
@@ -755,7 +771,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
             coot_two_sum(s[v], c[v], coot_f(x));
           }
       }
-      for (; j < je; ++j) {
+      for (; j < je; j += COOT_CG) {
         COOT_REAL xv[4][COOT_VEC];
         coot_load_vec(p, j, i0, xv);
 #pragma unroll
@@ -766,7 +782,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       }
     } else {
 #pragma unroll 1
-      for (coot_i64 j = jb; j < je; ++j) {
+      for (coot_i64 j = jb + ty; j < je; j += COOT_CG) {
 #pragma unroll
         for (int v = 0; v < COOT_VEC; ++v) {
           if (i0 + v < p.n_rows) {
@@ -777,34 +793,67 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
         }
       }
     }
+    // column groups in order -> the block's sum of each row over the chunk
+#pragma unroll
+    for (int v = 0; v < COOT_VEC; ++v) red[ty][tx * COOT_VEC + v] = coot_pair(s[v], c[v]);
+    __syncthreads();
+    double tot[COOT_VEC];
+    if (ty == 0) {
+#pragma unroll
+      for (int v = 0; v < COOT_VEC; ++v) {
+        double t = red[0][tx * COOT_VEC + v];
+#pragma unroll
+        for (int g = 1; g < COOT_CG; ++g) t += red[g][tx * COOT_VEC + v];
+        tot[v] = t;
+      }
+    }
     if (C == 1) {
+      if (ty == 0) {
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v)
+          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(tot[v]);
+      }
+      __syncthreads();  // red is rewritten by the next unit
+      continue;
+    }
+    double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
+    coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
+    if (ty == 0) {
 #pragma unroll
       for (int v = 0; v < COOT_VEC; ++v)
-        if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(coot_pair(s[v], c[v]));
-    } else {
-      double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
-      coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
-#pragma unroll
-      for (int v = 0; v < COOT_VEC; ++v)
-        if (i0 + v < p.n_rows) part[chunk * p.n_rows + i0 + v] = coot_pair(s[v], c[v]);
+        if (i0 + v < p.n_rows) part[chunk * p.n_rows + i0 + v] = tot[v];
       __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(cnt + panel, 1u) == (coot_u32)(C - 1));
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      // group g adds chunks g, g + CG, ... for its rows; then group order
+      double t[COOT_VEC];
+#pragma unroll
+      for (int v = 0; v < COOT_VEC; ++v) t[v] = 0.0;
+#pragma unroll 4
+      for (coot_i64 q = ty; q < C; q += COOT_CG) {
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v)
+          if (i0 + v < p.n_rows) t[v] += __ldcg(part + q * p.n_rows + i0 + v);
+      }
+#pragma unroll
+      for (int v = 0; v < COOT_VEC; ++v) red[ty][tx * COOT_VEC + v] = t[v];
       __syncthreads();
-      if (threadIdx.x == 0) is_last = (atomicAdd(cnt + panel, 1u) == (coot_u32)(C - 1));
-      __syncthreads();
-      if (is_last) {
-        __threadfence();
+      if (ty == 0) {
 #pragma unroll
         for (int v = 0; v < COOT_VEC; ++v) {
-          if (i0 + v < p.n_rows) {
-            double t = 0.0;
-            for (coot_i64 q = 0; q < C; ++q) t += __ldcg(part + q * p.n_rows + i0 + v);
-            ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(t);
-          }
+          double w = red[0][tx * COOT_VEC + v];
+#pragma unroll
+          for (int g = 1; g < COOT_CG; ++g) w += red[g][tx * COOT_VEC + v];
+          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(w);
         }
-        if (threadIdx.x == 0) cnt[panel] = 0u;
       }
-      __syncthreads();  // is_last is rewritten by the next unit
+      if (threadIdx.x == 0) cnt[panel] = 0u;
     }
+    __syncthreads();  // red and is_last are rewritten by the next unit
   }
 }
 #endif
