@@ -40,9 +40,13 @@ def cuda_home() -> str:
     raise RuntimeError("CUDA toolkit not found (set CUDA_HOME)")
 
 
+JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh"]
+
+
 def _embed_runtime() -> str:
-    """jit_rt.cuh as a C string in a generated translation unit."""
-    src = open(os.path.join(CSRC, "jit_rt.cuh"), encoding="utf-8").read()
+    """The device runtime (jit_rt.cuh and the per-kernel files, in order) as
+    one C string in a generated translation unit."""
+    src = "".join(open(os.path.join(CSRC, f), encoding="utf-8").read() + "\n" for f in JIT_SOURCES)
     out = os.path.join(BUILD, "jit_rt_embed.cpp")
     body = ['// generated from jit_rt.cuh by build.py\nextern "C" const char* coot_jit_rt_source =\n']
     # raw string pieces well below compiler limits on literal length

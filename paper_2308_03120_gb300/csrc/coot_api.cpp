@@ -247,7 +247,7 @@ static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, u
   spec.block = l.block;
   spec.nc = !aliased;
   const Compiled* c = nullptr;
-  coot_status s = get_kernel(generate_source(t, spec), spec, &c);
+  coot_status s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;
   coot_params_host p;
   fill_io(&p, v, n_in);
@@ -307,7 +307,7 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   spec.block = l.block;
   spec.nc = true;
   const Compiled* c = nullptr;
-  s = get_kernel(generate_source(t, spec), spec, &c);
+  s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;
   coot_params_host p;
   fill_io(&p, v, n_in);
@@ -537,8 +537,13 @@ struct WorkUnit {
 static_assert(sizeof(coot_batch_item) == 14 * 8, "coot_batch_item layout");
 static_assert(sizeof(WorkUnit) == 16, "work unit layout");
 
-// columns of one matrix handled by one warp
-static int64_t cols_per_unit(int64_t n_rows) { return n_rows >= 32 ? 1 : (n_rows == 0 ? 32 : 32 / n_rows); }
+// Columns of one matrix in one work unit (one block): about 8192 elements,
+// whole columns, at least one column per warp-slot.
+static int64_t cols_per_unit(int64_t n_rows) {
+  const int64_t target = 8192;
+  if (n_rows <= 0) return target;
+  return std::max<int64_t>(1, target / n_rows);
+}
 
 coot_status coot_batch_plan_size(const coot_batch_item* items, int n_items, size_t* bytes, int64_t* n_work) {
   clear_error();
@@ -612,7 +617,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.unroll = 4;
   spec.block = 256;
   const Compiled* c = nullptr;
-  s = get_kernel(generate_source(t, spec), spec, &c);
+  s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;
   coot_params_host p;
   std::memset(&p, 0, sizeof p);
@@ -620,8 +625,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   p.split = n_items;
   p.n_work = n_work;
   p.rows_per_split = colsum_dtype;
-  const int64_t warps = spec.block / 32;
-  return launch(c, (n_work + warps - 1) / warps, INT32_MAX, spec.block, &p, stream);
+  return launch(c, n_work, INT32_MAX, spec.block, &p, stream);
 }
 
 coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws, size_t ws_bytes, void* stream) {

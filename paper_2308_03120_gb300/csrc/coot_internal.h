@@ -70,6 +70,10 @@ struct Compiled {
 // Returns the compiled kernel for `source`, compiling it with NVRTC on a
 // miss (memory cache, then the on-disk cache, then NVRTC).
 coot_status get_kernel(const std::string& source, const KernelSpec& spec, const Compiled** out);
+
+// The kernel of (tree, spec): a lookup by digest first, then get_kernel on
+// the generated source.
+coot_status kernel_for(const Tree& t, const KernelSpec& spec, const Compiled** out);
 void drop_kernels();
 
 // Device facts cached by coot_init.

@@ -182,7 +182,40 @@ coot_status get_kernel(const std::string& source, const KernelSpec& spec, const 
   return COOT_OK;
 }
 
+// Calls after the first with the same tree and kernel shape skip source
+// generation: the kernel is found by a digest of the tree bytes and of
+// every field of the spec.
+static std::mutex g_fast_mu;
+static std::unordered_map<uint64_t, const Compiled*> g_fast;
+
+static uint64_t spec_key(const Tree& t, const KernelSpec& s) {
+  const int64_t f[] = {s.kind, s.in_dtype[0], s.in_dtype[1], s.in_dtype[2], s.in_dtype[3], s.out_dtype,
+                       s.store, (int64_t)s.heads, s.vec, s.unroll, s.block, s.nc, g_dev.id};
+  return fnv1a(f, sizeof f, t.hash);
+}
+
+coot_status kernel_for(const Tree& t, const KernelSpec& spec, const Compiled** out) {
+  const uint64_t key = spec_key(t, spec);
+  {
+    std::lock_guard<std::mutex> lock(g_fast_mu);
+    auto it = g_fast.find(key);
+    if (it != g_fast.end()) {
+      *out = it->second;
+      return COOT_OK;
+    }
+  }
+  coot_status s = get_kernel(generate_source(t, spec), spec, out);
+  if (s != COOT_OK) return s;
+  std::lock_guard<std::mutex> lock(g_fast_mu);
+  g_fast[key] = *out;
+  return COOT_OK;
+}
+
 void drop_kernels() {
+  {
+    std::lock_guard<std::mutex> lock(g_fast_mu);
+    g_fast.clear();
+  }
   std::lock_guard<std::mutex> lock(g_mu);
   g_kernels.clear();  // library handles stay loaded until the process exits
 }
@@ -194,7 +227,11 @@ coot_status init_device(int dev, unsigned flags) {
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, dev);
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
-  if (g_init && g_dev.id != dev) g_kernels.clear();
+  if (g_init && g_dev.id != dev) {
+    std::lock_guard<std::mutex> fast(g_fast_mu);
+    g_fast.clear();
+    g_kernels.clear();
+  }
   g_dev.id = dev;
   g_dev.sm_count = prop.multiProcessorCount;
   g_dev.cc_major = prop.major;

@@ -339,6 +339,20 @@ __device__ __forceinline__ COOT_REAL coot_abs(COOT_REAL y) {
   }
 }
 
+// Pairwise sum of V values (what = 0: the values, 1: their squares, each
+// rounded separately, 2: their magnitudes): ((y0 + y1) + (y2 + y3)) + ...
+template <int V>
+__device__ __forceinline__ COOT_REAL coot_pairwise(const COOT_REAL* y, int what) {
+  COOT_REAL t[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) t[v] = what == 0 ? y[v] : (what == 1 ? coot_sq(y[v]) : coot_abs(y[v]));
+#pragma unroll
+  for (int w = 1; w < V; w *= 2)
+#pragma unroll
+    for (int v = 0; v + w < V; v += 2 * w) t[v] = t[v] + t[v + w];
+  return t[0];
+}
+
 // ---------------------------------------------------------------- accumulators
 
 #ifndef COOT_HEADS
@@ -369,6 +383,23 @@ struct coot_acc {
     if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y);
     if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
     if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
+  }
+  // V consecutive values: the sums of the vector are formed pairwise (a
+  // tree of depth log2 V), then added to the running pair with one TwoSum,
+  // which keeps the per-element cost low enough for 2-byte inputs to stay
+  // memory-bound; the extrema are taken element by element
+  template <int V>
+  __device__ __forceinline__ void add_vec(const COOT_REAL* y) {
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, coot_pairwise<V>(y, 0));
+    if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
+      if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
+      if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
+      if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y[v]));
+    }
   }
   // per-head values as FP64, in head-bit order
   __device__ __forceinline__ void values(double* v) const {
@@ -477,383 +508,5 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
     }
   }
   if (threadIdx.x == 0) *(coot_u32*)(p.ws + COOT_WS_COUNTER_OFF) = 0u;
-}
-#endif
-
-// ================================================================ kind 0/1: evaluation and full reductions
-
-#if COOT_KIND == 0 || COOT_KIND == 1
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  constexpr coot_i64 TILE = (coot_i64)COOT_BLOCK * COOT_VEC * COOT_UNROLL;
-  const coot_i64 upc = (p.n_rows + TILE - 1) / TILE;  // tiles per column
-  const coot_i64 units = upc * p.n_cols;
-  typedef typename coot_st<COOT_TO>::T TO;
-  coot_acc acc;
-  acc.init();
-  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
-    const coot_i64 j = u / upc;
-    const coot_i64 r0 = (u - j * upc) * TILE;
-    if (r0 + TILE <= p.n_rows) {
-      COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
-#pragma unroll
-      for (int k = 0; k < COOT_UNROLL; ++k)
-        coot_load_vec(p, j, r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC, xv[k]);
-#pragma unroll
-      for (int k = 0; k < COOT_UNROLL; ++k) {
-        COOT_REAL y[COOT_VEC];
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) {
-          const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
-          y[v] = coot_f(x);
-          acc.add(y[v]);
-        }
-#if COOT_STORE
-        coot_vstore<COOT_TO, COOT_VEC>(
-            (TO*)p.out + (j * p.ld_out + r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC), y);
-#endif
-      }
-    } else {
-      // the ragged end of a column, one element at a time
-#pragma unroll 1
-      for (int k = 0; k < COOT_UNROLL; ++k) {
-#pragma unroll 1
-        for (int v = 0; v < COOT_VEC; ++v) {
-          const coot_i64 row = r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC + v;
-          if (row < p.n_rows) {
-            COOT_REAL x[4];
-            coot_load_one(p, j, row, x);
-            const COOT_REAL y = coot_f(x);
-            acc.add(y);
-#if COOT_STORE
-            coot_sstore<COOT_TO>((TO*)p.out + (j * p.ld_out + row), y);
-#endif
-          }
-        }
-      }
-    }
-  }
-#if COOT_NHEADS > 0
-  coot_finish_full(acc, p);
-#endif
-}
-#endif
-
-// ================================================================ kind 2: column sums (dim = 0)
-
-// One warp per unit u = (column j, segment s): rows [s R, min((s + 1) R,
-// n_rows)) of column j with R = p.rows_per_split (a multiple of the warp
-// tile), p.split segments per column.  No block-level barrier is needed;
-// with several segments per column the segment sums go to the workspace and
-// the last warp of a column to arrive adds them in segment order.
-#if COOT_KIND == 2
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  constexpr coot_i64 WT = (coot_i64)32 * COOT_VEC * COOT_UNROLL;  // rows per warp tile
-  typedef typename coot_st<COOT_TO>::T TO;
-  const int lane = threadIdx.x & 31;
-  const coot_i64 S = p.split;
-  const coot_i64 units = p.n_cols * S;
-  const coot_i64 n_warps = (coot_i64)gridDim.x * COOT_WARPS;
-  for (coot_i64 u = (coot_i64)blockIdx.x * COOT_WARPS + (threadIdx.x >> 5); u < units; u += n_warps) {
-    const coot_i64 j = u / S;
-    const coot_i64 s = u - j * S;
-    const coot_i64 rb = s * p.rows_per_split;
-    const coot_i64 re = min(p.n_rows, rb + p.rows_per_split);
-    COOT_REAL acc = 0, accc = 0;
-    coot_i64 r0 = rb;
-    for (; r0 + WT <= re; r0 += WT) {
-      COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
-#pragma unroll
-      for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j, r0 + ((coot_i64)k * 32 + lane) * COOT_VEC, xv[k]);
-#pragma unroll
-      for (int k = 0; k < COOT_UNROLL; ++k)
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) {
-          const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
-          coot_two_sum(acc, accc, coot_f(x));
-        }
-    }
-#pragma unroll 1
-    for (coot_i64 row = r0 + lane; row < re; row += 32) {
-      COOT_REAL x[4];
-      coot_load_one(p, j, row, x);
-      coot_two_sum(acc, accc, coot_f(x));
-    }
-    double v = coot_pair(acc, accc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-      if (S == 1) {
-        ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(v);
-      } else {
-        double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
-        coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
-        part[j * S + s] = v;
-        __threadfence();
-        if (atomicAdd(cnt + j, 1u) == (coot_u32)(S - 1)) {
-          __threadfence();
-          double t = 0.0;
-          for (coot_i64 q = 0; q < S; ++q) t += __ldcg(part + j * S + q);
-          ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(t);
-          cnt[j] = 0u;
-        }
-      }
-    }
-  }
-}
-#endif
-
-// ================================================================ kind 4: batched evaluation
-
-// One matrix of a batch (the layout of coot_batch_item in coot.h; every
-// field is 8 bytes).
-struct coot_batch_item_d {
-  const void* in[4];
-  coot_i64 ld_in[4];
-  void* out;
-  coot_i64 ld_out;
-  void* colsum;
-  coot_i64 ld_colsum;
-  coot_i64 n_rows;
-  coot_i64 n_cols;
-};
-
-// One unit of the work list: columns [col0, col0 + n_cols) of one matrix,
-// handled by one warp.  Matrices with at least 32 rows give one column per
-// unit; shorter columns are packed, floor(32 / n_rows) per unit.
-struct coot_work_d {
-  int item;
-  int col0;
-  int n_cols;
-  int pad;
-};
-
-#if COOT_KIND == 4
-__device__ __forceinline__ void coot_load_item(const coot_batch_item_d& it, coot_i64 j, coot_i64 row,
-                                               COOT_REAL (&x)[4]) {
-#define COOT_LOAD_B(I)                                                                    \
-  if constexpr (I < COOT_NIN) {                                                           \
-    constexpr int S = coot_in_code<I>::S;                                                 \
-    typedef typename coot_st<S>::T T;                                                     \
-    x[I] = coot_sload<S>((const T*)it.in[I] + (j * it.ld_in[I] + row));                  \
-  } else {                                                                                \
-    x[I] = (COOT_REAL)0;                                                                  \
-  }
-  COOT_LOAD_B(0)
-  COOT_LOAD_B(1)
-  COOT_LOAD_B(2)
-  COOT_LOAD_B(3)
-#undef COOT_LOAD_B
-}
-
-// p.plan: items (p.split of them) followed by the work list (p.n_work units).
-// COOT_TO is the storage code of the element-wise outputs; the column sums
-// are stored in the storage code given by p.rows_per_split (0 FP32, 3 FP64).
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  __shared__ double wbuf[COOT_WARPS][32];
-  typedef typename coot_st<COOT_TO>::T TO;
-  const coot_batch_item_d* items = (const coot_batch_item_d*)p.plan;
-  const coot_work_d* work = (const coot_work_d*)(items + p.split);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const coot_i64 n_warps = (coot_i64)gridDim.x * COOT_WARPS;
-  const bool sum64 = p.rows_per_split == 3;
-  for (coot_i64 w = (coot_i64)blockIdx.x * COOT_WARPS + warp; w < p.n_work; w += n_warps) {
-    const coot_work_d wk = work[w];
-    const coot_batch_item_d it = items[wk.item];
-    const coot_i64 R = it.n_rows;
-    if (R >= 32) {
-      const coot_i64 j = wk.col0;
-      COOT_REAL s = 0, c = 0;
-      for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
-        COOT_REAL xv[COOT_UNROLL][4];
-#pragma unroll
-        for (int q = 0; q < COOT_UNROLL; ++q) {
-          const coot_i64 r = r0 + 32 * q + lane;
-          if (r < R) coot_load_item(it, j, r, xv[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < COOT_UNROLL; ++q) {
-          const coot_i64 r = r0 + 32 * q + lane;
-          if (r < R) {
-            const COOT_REAL y = coot_f(xv[q]);
-            if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
-            coot_two_sum(s, c, y);
-          }
-        }
-      }
-      if (it.colsum) {
-        double v = coot_pair(s, c);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-          if (sum64) {
-            ((double*)it.colsum)[j * it.ld_colsum] = v;
-          } else {
-            ((float*)it.colsum)[j * it.ld_colsum] = (float)v;
-          }
-        }
-      }
-    } else {
-      // wk.n_cols short columns side by side: lane -> (column, row)
-      const int k = wk.n_cols;
-      const int Ri = (int)R;
-      double y64 = 0.0;
-      if (lane < k * Ri) {
-        const int cl = lane / Ri, r = lane - cl * Ri;
-        const coot_i64 j = wk.col0 + cl;
-        COOT_REAL x[4];
-        coot_load_item(it, j, r, x);
-        const COOT_REAL y = coot_f(x);
-        if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
-        y64 = (double)y;
-      }
-      if (it.colsum) {
-        wbuf[warp][lane] = y64;
-        __syncwarp();
-        if (lane < k) {
-          double t = 0.0;
-          for (int r = 0; r < Ri; ++r) t += wbuf[warp][lane * Ri + r];
-          const coot_i64 j = wk.col0 + lane;
-          if (sum64) {
-            ((double*)it.colsum)[j * it.ld_colsum] = t;
-          } else {
-            ((float*)it.colsum)[j * it.ld_colsum] = (float)t;
-          }
-        }
-        __syncwarp();
-      }
-    }
-  }
-}
-#endif
-
-// ================================================================ kind 3: row sums (dim = 1)
-
-// A block is COOT_RT row threads x (COOT_BLOCK / COOT_RT) column groups and
-// owns a panel of COOT_RT * COOT_VEC rows over one chunk of columns; column
-// group g takes the chunk's columns g, g + CG, ... with COOT_UNROLL of them
-// in flight.  The groups are added in shared memory in group order; with
-// several chunks the chunk sums go to the workspace and the last block of a
-// panel to arrive adds them (each group a strided subset of the chunks,
-// then the groups in order), so the order is fixed.
-#if COOT_KIND == 3
-#define COOT_RT 64
-#define COOT_CG (COOT_BLOCK / COOT_RT)
-#define COOT_PANEL (COOT_RT * COOT_VEC)
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  __shared__ double red[COOT_CG][COOT_PANEL];
-  __shared__ int is_last;
-  typedef typename coot_st<COOT_TO>::T TO;
-  const int tx = threadIdx.x % COOT_RT, ty = threadIdx.x / COOT_RT;
-  const coot_i64 n_panels = (p.n_rows + COOT_PANEL - 1) / COOT_PANEL;
-  const coot_i64 C = p.split;                               // column chunks
-  const coot_i64 Q = (p.n_cols + C - 1) / C;                // columns per chunk
-  const coot_i64 units = n_panels * C;
-  for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
-    const coot_i64 chunk = u / n_panels;
-    const coot_i64 panel = u - chunk * n_panels;
-    const coot_i64 i0 = panel * COOT_PANEL + (coot_i64)tx * COOT_VEC;
-    const coot_i64 jb = chunk * Q;
-    const coot_i64 je = min(p.n_cols, jb + Q);
-    COOT_REAL s[COOT_VEC], c[COOT_VEC];
-#pragma unroll
-    for (int v = 0; v < COOT_VEC; ++v) s[v] = c[v] = 0;
-    if (panel * COOT_PANEL + COOT_PANEL <= p.n_rows) {
-      coot_i64 j = jb + ty;
-      for (; j + (coot_i64)(COOT_UNROLL - 1) * COOT_CG < je; j += (coot_i64)COOT_UNROLL * COOT_CG) {
-        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
-#pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j + (coot_i64)k * COOT_CG, i0, xv[k]);
-#pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k)
-#pragma unroll
-          for (int v = 0; v < COOT_VEC; ++v) {
-            const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
-            coot_two_sum(s[v], c[v], coot_f(x));
-          }
-      }
-      for (; j < je; j += COOT_CG) {
-        COOT_REAL xv[4][COOT_VEC];
-        coot_load_vec(p, j, i0, xv);
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) {
-          const COOT_REAL x[4] = {xv[0][v], xv[1][v], xv[2][v], xv[3][v]};
-          coot_two_sum(s[v], c[v], coot_f(x));
-        }
-      }
-    } else {
-#pragma unroll 1
-      for (coot_i64 j = jb + ty; j < je; j += COOT_CG) {
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) {
-          if (i0 + v < p.n_rows) {
-            COOT_REAL x[4];
-            coot_load_one(p, j, i0 + v, x);
-            coot_two_sum(s[v], c[v], coot_f(x));
-          }
-        }
-      }
-    }
-    // column groups in order -> the block's sum of each row over the chunk
-#pragma unroll
-    for (int v = 0; v < COOT_VEC; ++v) red[ty][tx * COOT_VEC + v] = coot_pair(s[v], c[v]);
-    __syncthreads();
-    double tot[COOT_VEC];
-    if (ty == 0) {
-#pragma unroll
-      for (int v = 0; v < COOT_VEC; ++v) {
-        double t = red[0][tx * COOT_VEC + v];
-#pragma unroll
-        for (int g = 1; g < COOT_CG; ++g) t += red[g][tx * COOT_VEC + v];
-        tot[v] = t;
-      }
-    }
-    if (C == 1) {
-      if (ty == 0) {
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v)
-          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(tot[v]);
-      }
-      __syncthreads();  // red is rewritten by the next unit
-      continue;
-    }
-    double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
-    coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
-    if (ty == 0) {
-#pragma unroll
-      for (int v = 0; v < COOT_VEC; ++v)
-        if (i0 + v < p.n_rows) part[chunk * p.n_rows + i0 + v] = tot[v];
-      __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(cnt + panel, 1u) == (coot_u32)(C - 1));
-    __syncthreads();
-    if (is_last) {
-      __threadfence();
-      // group g adds chunks g, g + CG, ... for its rows; then group order
-      double t[COOT_VEC];
-#pragma unroll
-      for (int v = 0; v < COOT_VEC; ++v) t[v] = 0.0;
-#pragma unroll 4
-      for (coot_i64 q = ty; q < C; q += COOT_CG) {
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v)
-          if (i0 + v < p.n_rows) t[v] += __ldcg(part + q * p.n_rows + i0 + v);
-      }
-#pragma unroll
-      for (int v = 0; v < COOT_VEC; ++v) red[ty][tx * COOT_VEC + v] = t[v];
-      __syncthreads();
-      if (ty == 0) {
-#pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) {
-          double w = red[0][tx * COOT_VEC + v];
-#pragma unroll
-          for (int g = 1; g < COOT_CG; ++g) w += red[g][tx * COOT_VEC + v];
-          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(w);
-        }
-      }
-      if (threadIdx.x == 0) cnt[panel] = 0u;
-    }
-    __syncthreads();  // red and is_last are rewritten by the next unit
-  }
 }
 #endif
