@@ -575,9 +575,12 @@ def run_batched(args):
             coot.coot_expr_eval(tree, ins, om, stream=s)
             coot.coot_sum_dim(tree, ins, 0, cm, ws=ws, stream=s)
 
-    ms_per = _timed(torch, stream, per_matrix, max(2, args.steps // 10), 1)
-    gp = _graph(torch, per_matrix)
-    ms_per_graph = _timed(torch, stream, gp.replay, max(2, args.steps // 10), 1)
+    if args.no_per_matrix:
+        ms_per = ms_per_graph = float("nan")
+    else:
+        ms_per = _timed(torch, stream, per_matrix, max(2, args.steps // 10), 1)
+        gp = _graph(torch, per_matrix)
+        ms_per_graph = _timed(torch, stream, gp.replay, max(2, args.steps // 10), 1)
     elems = int(sizes.sum())
     nbytes = elems * 4 * 4 + int(cols.sum()) * 4
     peak, kind = peaks()
@@ -605,6 +608,7 @@ def main():
     ap.add_argument("--n", type=int, default=8192, help="matrix order (8192 is the workload; smaller for profiling)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
     ap.add_argument("--workload", default="matrices",
                     choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched"],
                     help="matrices is the headline line; the others print their own line")

@@ -76,7 +76,9 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       sit = items[swk.item];
     }
     __syncthreads();
-    const coot_batch_item_d& it = sit;
+    // a register copy: read from shared memory, the pointers would be
+    // reloaded after every store and serialise the loads
+    const coot_batch_item_d it = sit;
     const coot_i64 R = it.n_rows;
     const coot_i64 c0 = swk.col0, nc = swk.n_cols;
     if (R >= 32) {

@@ -34,7 +34,8 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
           const COOT_REAL x[4] = {xv[k][0][v], xv[k][1][v], xv[k][2][v], xv[k][3][v]};
           y[v] = coot_f(x);
         }
-        coot_two_sum(acc, accc, coot_pairwise<COOT_VEC>(y, 0));
+#pragma unroll
+        for (int v = 0; v < COOT_VEC; ++v) coot_two_sum(acc, accc, y[v]);
       }
     }
 #pragma unroll 1

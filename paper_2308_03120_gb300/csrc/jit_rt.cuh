@@ -384,17 +384,19 @@ struct coot_acc {
     if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
     if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
   }
-  // V consecutive values: the sums of the vector are formed pairwise (a
-  // tree of depth log2 V), then added to the running pair with one TwoSum,
-  // which keeps the per-element cost low enough for 2-byte inputs to stay
-  // memory-bound; the extrema are taken element by element
+  // V consecutive values.  The plain sum adds every value with TwoSum (no
+  // rounding is lost however the terms cancel).  Sums of squares and of
+  // magnitudes have no cancellation: their vector is added pairwise (a tree
+  // of depth log2 V) and the result enters the running pair with one
+  // TwoSum, which keeps 2-byte inputs memory-bound.  Extrema are taken
+  // element by element.
   template <int V>
   __device__ __forceinline__ void add_vec(const COOT_REAL* y) {
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, coot_pairwise<V>(y, 0));
     if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
     if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
 #pragma unroll
     for (int v = 0; v < V; ++v) {
+      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
