@@ -324,7 +324,7 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     const int64_t wt = 32LL * l.vec * l.unroll;  // rows per warp tile
     const int64_t target = 3 * resident * warps;
     int64_t S = 1;
-    if (Cn < target && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
+    if (4 * Cn < 3 * resident * warps && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
       S = std::min<int64_t>((target + Cn - 1) / Cn, (R + wt - 1) / wt);
       S = std::min<int64_t>(S, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(Cn, 1))));
       S = std::max<int64_t>(S, 1);
@@ -344,7 +344,9 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     int64_t C = std::max<int64_t>(1, (2 * resident + n_panels - 1) / n_panels);
     C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));
     C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);
-    C = std::min<int64_t>(C, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(R, 1))));
+    // a chunk partial is a double-word pair of the compute type per row
+    const int64_t entry = 2 * (t.compute == COOT_F64 ? 8 : 4);
+    C = std::min<int64_t>(C, (int64_t)(part_bytes / (entry * std::max<int64_t>(R, 1))));
     if (n_panels > COOT_WS_MAX_COUNTERS) C = 1;
     C = std::max<int64_t>(C, 1);
     p.split = C;

@@ -61,7 +61,7 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // n_rows) columns side by side in one warp, summed through shared memory
 // in row order.
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  __shared__ double wbuf[COOT_WARPS][32];
+  __shared__ COOT_REAL wbuf[COOT_WARPS][32];
   __shared__ coot_batch_item_d sit;
   __shared__ coot_work_d swk;
   typedef typename coot_st<COOT_TO>::T TO;
@@ -103,10 +103,10 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
           }
         }
         if (it.colsum) {
-          double v = coot_pair(s, c);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) coot_store_colsum(it, j, v, sum64);
+          COOT_REAL vh, vl;
+          coot_dw_norm(s, c, vh, vl);
+          coot_dw_warp_sum(vh, vl);
+          if (lane == 0) coot_store_colsum(it, j, coot_dw_to_double(vh, vl), sum64);
         }
       }
     } else {
@@ -115,23 +115,22 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       const int k = Ri > 0 ? 32 / Ri : 32;
       for (coot_i64 g0 = (coot_i64)warp * k; g0 < nc; g0 += (coot_i64)COOT_WARPS * k) {
         const int kk = (int)min((coot_i64)k, nc - g0);
-        double y64 = 0.0;
+        COOT_REAL y = 0;
         if (lane < kk * Ri) {
           const int cl = lane / Ri, r = lane - cl * Ri;
           const coot_i64 j = c0 + g0 + cl;
           COOT_REAL x[4];
           coot_load_item(it, j, r, x);
-          const COOT_REAL y = coot_f(x);
+          y = coot_f(x);
           if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
-          y64 = (double)y;
         }
         if (it.colsum) {
-          wbuf[warp][lane] = y64;
+          wbuf[warp][lane] = y;
           __syncwarp();
           if (lane < kk) {
-            double t = 0.0;
-            for (int r = 0; r < Ri; ++r) t += wbuf[warp][lane * Ri + r];
-            coot_store_colsum(it, c0 + g0 + lane, t, sum64);
+            COOT_REAL t = 0, tc = 0;
+            for (int r = 0; r < Ri; ++r) coot_two_sum(t, tc, wbuf[warp][lane * Ri + r]);
+            coot_store_colsum(it, c0 + g0 + lane, coot_pair(t, tc), sum64);
           }
           __syncwarp();
         }

@@ -44,10 +44,11 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       coot_load_one(p, j, row, x);
       coot_two_sum(acc, accc, coot_f(x));
     }
-    double v = coot_pair(acc, accc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    COOT_REAL vh, vl;
+    coot_dw_norm(acc, accc, vh, vl);
+    coot_dw_warp_sum(vh, vl);
     if (lane == 0) {
+      const double v = coot_dw_to_double(vh, vl);
       if (S == 1) {
         ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(v);
       } else {

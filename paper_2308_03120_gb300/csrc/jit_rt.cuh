@@ -24,9 +24,10 @@
 // of one column for evaluation and column sums, a panel of rows times a
 // range of columns for row sums), so any grid size covers any shape.
 // Reductions add in FP32 (or FP64) with TwoSum compensation per thread,
-// then combine per-thread results in FP64 through warp shuffles, shared
-// memory and one FP64 partial per block; the last block to finish combines
-// the partials in a fixed order, so a result does not depend on timing.
+// then combine per-thread results as double-word numbers through warp
+// shuffles and shared memory into one FP64 partial per block; the last
+// block to finish combines the partials in FP64 in a fixed order, so a
+// result does not depend on timing.
 
 typedef unsigned short coot_u16;
 typedef unsigned int coot_u32;
@@ -315,6 +316,69 @@ __device__ __forceinline__ void coot_two_sum(COOT_REAL& s, COOT_REAL& c, COOT_RE
   c += e;
 }
 
+// ---------------------------------------------------------------- double-word sums
+//
+// Values that are combined across threads travel as unevaluated pairs
+// (hi, lo) of the compute type ("double-word" numbers): on this GPU FP64
+// arithmetic runs at 1/64 of the FP32 rate, so FP64 is kept for the one
+// conversion per block and the final combine of the block partials.  The
+// pair addition is the accurate double-word sum of Joldes, Muller and
+// Popescu ("Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", ACM TOMS 2017), relative error about 3u^2.
+
+// s + e = a + b exactly, if |a| >= |b| or a == 0 (Dekker's Fast2Sum)
+__device__ __forceinline__ void coot_fast_two(COOT_REAL a, COOT_REAL b, COOT_REAL& s, COOT_REAL& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// s + e = a + b exactly, any a, b (Knuth's TwoSum)
+__device__ __forceinline__ void coot_two(COOT_REAL a, COOT_REAL b, COOT_REAL& s, COOT_REAL& e) {
+  s = a + b;
+  const COOT_REAL bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// (xh, xl) += (yh, yl); both pairs normalised (|lo| <= ulp(hi) / 2).  A
+// non-finite high part is passed on with a zero low part.
+__device__ __forceinline__ void coot_dw_add(COOT_REAL& xh, COOT_REAL& xl, COOT_REAL yh, COOT_REAL yl) {
+  COOT_REAL sh, sl, th, tl, vh, vl, zh, zl;
+  coot_two(xh, yh, sh, sl);
+  coot_two(xl, yl, th, tl);
+  sl = sl + th;
+  coot_fast_two(sh, sl, vh, vl);
+  vl = vl + tl;
+  coot_fast_two(vh, vl, zh, zl);
+  const bool fin = isfinite(sh);
+  xh = fin ? zh : sh;
+  xl = fin ? zl : (COOT_REAL)0;
+}
+
+// a running (sum, compensation) pair as a normalised double-word number
+__device__ __forceinline__ void coot_dw_norm(COOT_REAL s, COOT_REAL c, COOT_REAL& h, COOT_REAL& l) {
+  coot_two(s, c, h, l);
+  if (!isfinite(s)) {
+    h = s;
+    l = (COOT_REAL)0;
+  }
+}
+
+// warp sum of double-word numbers (fixed shuffle tree; the result is valid
+// in lane 0)
+__device__ __forceinline__ void coot_dw_warp_sum(COOT_REAL& h, COOT_REAL& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const COOT_REAL yh = __shfl_down_sync(0xffffffffu, h, o);
+    const COOT_REAL yl = __shfl_down_sync(0xffffffffu, l, o);
+    coot_dw_add(h, l, yh, yl);
+  }
+}
+
+__device__ __forceinline__ double coot_dw_to_double(COOT_REAL h, COOT_REAL l) {
+  const double hd = (double)h;
+  return isfinite(hd) ? hd + (double)l : hd;
+}
+
 // the pair as one FP64 value; once the sum is infinite or NaN the
 // compensation carries inf - inf and is dropped
 __device__ __forceinline__ double coot_pair(COOT_REAL s, COOT_REAL c) {
@@ -404,16 +468,18 @@ struct coot_acc {
     }
   }
   // per-head values as FP64, in head-bit order
-  __device__ __forceinline__ void values(double* v) const {
+  // per-head values as double-word pairs in head-bit order (sums
+  // normalised; extrema as (value, 0))
+  __device__ __forceinline__ void values(COOT_REAL* h, COOT_REAL* l) const {
     int k = 0;
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) v[k++] = coot_pair(s, sc);
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMSQ) != 0) v[k++] = coot_pair(q, qc);
-    if constexpr ((COOT_HEADS & COOT_HEAD_NORM2) != 0) v[k++] = coot_pair(q, qc);
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) v[k++] = coot_pair(a, ac);
-    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) v[k++] = (double)mn;
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) v[k++] = (double)mx;
-    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) v[k++] = (double)mna;
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) v[k++] = (double)mxa;
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) { coot_dw_norm(s, sc, h[k], l[k]); ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMSQ) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_NORM2) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) { coot_dw_norm(a, ac, h[k], l[k]); ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) { h[k] = mn; l[k] = 0; ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) { h[k] = mx; l[k] = 0; ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) { h[k] = mna; l[k] = 0; ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) { h[k] = mxa; l[k] = 0; ++k; }
     (void)k;
   }
 };
@@ -437,38 +503,48 @@ __device__ __forceinline__ double coot_identity(unsigned bit) {
   return 0.0;
 }
 
-// FP64 sum of one value per thread across the block (fixed shuffle tree);
-// the result is valid in thread 0.  All threads of the block must call it.
-__device__ __forceinline__ double coot_block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();  // red may still be read from a previous call
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = lane < COOT_WARPS ? red[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  }
-  return v;
+#if COOT_NHEADS > 0
+__device__ __forceinline__ COOT_REAL coot_identity_r(unsigned bit) {
+  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return (COOT_REAL)COOT_INF_F;
+  if (bit == COOT_HEAD_MAX) return -(COOT_REAL)COOT_INF_F;
+  return (COOT_REAL)0;
 }
 
-#if COOT_NHEADS > 0
-// Block-level combine of every head, one FP64 partial per block and head,
-// and the last-arriving block's ordered combine into p.res.
+// head `bit`'s combine of two double-word values
+__device__ __forceinline__ void coot_combine_dw(unsigned bit, COOT_REAL& h, COOT_REAL& l, COOT_REAL yh, COOT_REAL yl) {
+  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) {
+    h = coot_min(h, yh);
+  } else if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_MAXABS) {
+    h = coot_max(h, yh);
+  } else {
+    coot_dw_add(h, l, yh, yl);
+  }
+}
+
+// Block-level combine of every head in double-word arithmetic, one FP64
+// partial per block and head, and the last-arriving block's ordered FP64
+// combine of the partials into p.res.
 __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
-  __shared__ double red[COOT_NHEADS][COOT_WARPS];
+  __shared__ COOT_REAL red_h[COOT_NHEADS][COOT_WARPS];
+  __shared__ COOT_REAL red_l[COOT_NHEADS][COOT_WARPS];
+  __shared__ double red64[COOT_WARPS];
   __shared__ int is_last;
-  double v[COOT_NHEADS];
-  acc.values(v);
+  COOT_REAL h[COOT_NHEADS], l[COOT_NHEADS];
+  acc.values(h, l);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < COOT_NHEADS; ++k) {
     const unsigned bit = coot_head_bit(k);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] = coot_combine(bit, v[k], __shfl_down_sync(0xffffffffu, v[k], o));
-    if (lane == 0) red[k][warp] = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const COOT_REAL yh = __shfl_down_sync(0xffffffffu, h[k], o);
+      const COOT_REAL yl = __shfl_down_sync(0xffffffffu, l[k], o);
+      coot_combine_dw(bit, h[k], l[k], yh, yl);
+    }
+    if (lane == 0) {
+      red_h[k][warp] = h[k];
+      red_l[k][warp] = l[k];
+    }
   }
   __syncthreads();
   double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
@@ -476,10 +552,15 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
 #pragma unroll
     for (int k = 0; k < COOT_NHEADS; ++k) {
       const unsigned bit = coot_head_bit(k);
-      double w = lane < COOT_WARPS ? red[k][lane] : coot_identity(bit);
+      COOT_REAL wh = lane < COOT_WARPS ? red_h[k][lane] : coot_identity_r(bit);
+      COOT_REAL wl = lane < COOT_WARPS ? red_l[k][lane] : (COOT_REAL)0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
-      if (lane == 0) part[(coot_i64)k * gridDim.x + blockIdx.x] = w;
+      for (int o = 16; o > 0; o >>= 1) {
+        const COOT_REAL yh = __shfl_down_sync(0xffffffffu, wh, o);
+        const COOT_REAL yl = __shfl_down_sync(0xffffffffu, wl, o);
+        coot_combine_dw(bit, wh, wl, yh, yl);
+      }
+      if (lane == 0) part[(coot_i64)k * gridDim.x + blockIdx.x] = coot_dw_to_double(wh, wl);
     }
   }
   if (threadIdx.x == 0) {
@@ -491,7 +572,7 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
   if (!is_last) return;
   __threadfence();
   // the last block: every thread folds a strided subset of the partials in
-  // index order, then the block combines the thread results
+  // index order (FP64), then the block combines the thread results
   for (int k = 0; k < COOT_NHEADS; ++k) {
     const unsigned bit = coot_head_bit(k);
     double w = coot_identity(bit);
@@ -500,10 +581,10 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
     __syncthreads();
-    if (lane == 0) red[0][warp] = w;
+    if (lane == 0) red64[warp] = w;
     __syncthreads();
     if (warp == 0) {
-      w = lane < COOT_WARPS ? red[0][lane] : coot_identity(bit);
+      w = lane < COOT_WARPS ? red64[lane] : coot_identity(bit);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
       if (lane == 0) p.res[k] = (bit == COOT_HEAD_NORM2) ? sqrt(w) : w;

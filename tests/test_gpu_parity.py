@@ -132,6 +132,30 @@ def test_fp64_compute():
     _eval_case(synth.MAT_CHAIN, specs, 13, out_dtype="f64", compute="f64")
 
 
+def test_fp64_compute_reductions():
+    """FP64 trees: full reductions and sums along both dims (the per-thread
+    pairs and their combination run in FP64 double-word arithmetic)."""
+    r, c = 2051, 67
+    specs = [("f64", r, c, None, -1.0, 1.0)] * 3 + [("f64", r, c, None, 0.0, 2.0)]
+    ins = host_mats(specs, 19)
+    tree = serialize(synth.MAT_CHAIN, compute="f64")
+    dev = [to_dev(h) for h in ins]
+    res = coot.coot_expr_reduce(tree, dev, coot.HEAD_SUM | coot.HEAD_NORM2 | coot.HEAD_MIN | coot.HEAD_MAX).tolist()
+    o0, o1 = Out(1, c, "f64"), Out(r, 1, "f64")
+    coot.coot_sum_dim(tree, dev, 0, o0.mat)
+    coot.coot_sum_dim(tree, dev, 1, o1.mat)
+    torch.cuda.synchronize()
+    v = O.evaluate(tree, ins)
+    assert abs(res[0] - O.accu(tree, ins)) <= 1e-12 * float(np.sum(np.abs(v)))
+    assert abs(res[1] - O.norm(tree, ins, "fro")) <= 1e-12 * O.norm(tree, ins, "fro")
+    assert abs(res[2] - v.min()) <= 1e-13 and abs(res[3] - v.max()) <= 1e-13
+    for dim, o in ((0, o0), (1, o1)):
+        got = O.logical(o.host()).ravel()
+        want = O.sum_dim(tree, ins, dim)
+        scale = np.sum(np.abs(v), axis=dim)
+        assert np.all(np.abs(got - want) <= 1e-12 * scale), dim
+
+
 def test_in_place_update():
     """B = B + 3 A, the paper's Task 2 (B += 3 * A): the output is input 1."""
     n = 300_001
