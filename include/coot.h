@@ -188,6 +188,25 @@ int coot_version(void);
  * `max_rows` rows (any number of columns).  Host-only. */
 coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
 
+/* Launch shape of the kernels of one kind (0 element-wise / with heads,
+ * 1 reductions only, 2 column sums, 3 row sums, 4 batched) for the calls
+ * that follow ON THIS THREAD, for tuning and for the learned selection of
+ * launch shapes (not in the paper).  block: threads per block, 64..1024 in
+ * steps of 64, or 0 to drop the setting (back to the built-in choice);
+ * vec: elements per vector access (1, 2, 4, 8; 0 = widest the operands'
+ * alignment allows; a width they do not allow is lowered); unroll: vector
+ * accesses in flight per thread and input, 1..16 (0 = built-in); for the
+ * batched kind, rows in flight per lane; blocks_per_sm: cap on resident
+ * blocks per SM for the persistent grid (0 = occupancy limit); split:
+ * column sums: segments per column, row sums: column chunks (0 =
+ * chosen from the shape; capped by the workspace).  Host-only. */
+coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm,
+                                   int64_t split);
+
+/* Launch shape of the last kernel launched by a coot call on this thread
+ * (any out pointer may be NULL).  Host-only. */
+coot_status coot_last_launch(int* block, int* vec, int* unroll, int64_t* grid, int64_t* split);
+
 /* Validate a serialised tree without a GPU: on success *n_inputs receives
  * the tree's input count, *compute its compute dtype (COOT_F32 or COOT_F64)
  * and *hash a 64-bit FNV-1a digest of the bytes (the kernel-cache key).

@@ -22,7 +22,7 @@ from dataclasses import dataclass
 from . import _abi
 from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
                    HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM, HEAD_SUMABS, HEAD_SUMSQ,
-                   CootError, coot_mat)
+                   KIND_BATCHED, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSUM, CootError, coot_mat)
 from .expr import Expr, abs_, const, exp, log, serialize, sqrt, square, var
 
 __all__ = [
@@ -302,3 +302,19 @@ def coot_sum_rows_f32_static(a: Mat, out: Mat, stream=None) -> None:
     workspace, no allocation); n_rows <= 32768."""
     ca, co = a.c(), out.c()
     _abi.call("coot_sum_rows_f32_static", ctypes.byref(ca), ctypes.byref(co), _stream(stream))
+
+
+# ---------------------------------------------------------------- launch shapes
+
+def coot_set_launch_config(kind: int, block: int = 0, vec: int = 0, unroll: int = 0, blocks_per_sm: int = 0,
+                           split: int = 0) -> None:
+    """Launch shape for the kernels of `kind` on this thread (block = 0
+    restores the built-in choice)."""
+    _abi.call("coot_set_launch_config", kind, block, vec, unroll, blocks_per_sm, split)
+
+
+def coot_last_launch() -> dict:
+    b, v, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    g, s = ctypes.c_int64(), ctypes.c_int64()
+    _abi.call("coot_last_launch", ctypes.byref(b), ctypes.byref(v), ctypes.byref(u), ctypes.byref(g), ctypes.byref(s))
+    return {"block": b.value, "vec": v.value, "unroll": u.value, "grid": g.value, "split": s.value}

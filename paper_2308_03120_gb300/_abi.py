@@ -100,3 +100,7 @@ SIGNATURES.update({
 })
 
 SIGNATURES["coot_sum_rows_f32_static"] = (c_int, [_matp, _matp, c_void_p])
+
+SIGNATURES["coot_set_launch_config"] = (c_int, [c_int, c_int, c_int, c_int, c_int, c_int64])
+SIGNATURES["coot_last_launch"] = (c_int, [POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int64),
+                                          POINTER(c_int64)])

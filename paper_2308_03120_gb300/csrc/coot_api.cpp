@@ -160,16 +160,33 @@ static int pick_vec(const View& v, int max_vec = 8) {
 
 struct Launch {
   int vec = 1, unroll = 1, block = 256;
+  int blocks_per_sm = 0;  // 0: as many as fit
+  int64_t split = 0;      // 0: chosen from the shape
 };
+
+// A launch shape set by the caller for the calls that follow on this
+// thread (tuning, learned selection); block == 0 means "not set".
+static thread_local Launch g_override[5] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
+// The shape of the last launch on this thread.
+static thread_local Launch g_last;
+static thread_local int64_t g_last_grid = 0;
 
 static Launch heuristic(int kind, int n_in, const View& v) {
   Launch l;
+  const Launch& o = g_override[kind];
   l.vec = pick_vec(v);
   l.block = 256;
   if (kind == KIND_ROWSUM) {
     l.unroll = n_in >= 3 ? 4 : 8;
   } else {
     l.unroll = std::max(1, std::min(4, 8 / std::max(1, n_in)));
+  }
+  if (o.block) {
+    l.block = o.block;
+    if (o.vec) l.vec = pick_vec(v, o.vec);
+    if (o.unroll) l.unroll = o.unroll;
+    l.blocks_per_sm = o.blocks_per_sm;
+    l.split = o.split;
   }
   return l;
 }
@@ -185,16 +202,21 @@ static void fill_io(coot_params_host* p, const View& v, int n_in) {
   p->n_cols = v.n_cols;
 }
 
-static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, int block, coot_params_host* p,
+static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, const Launch& l, coot_params_host* p,
                           void* stream) {
-  int64_t grid = (int64_t)device().sm_count * std::max(1, c->max_blocks_per_sm);
+  int bps = std::max(1, c->max_blocks_per_sm);
+  if (l.blocks_per_sm > 0) bps = std::min(bps, l.blocks_per_sm);
+  int64_t grid = (int64_t)device().sm_count * bps;
   grid = std::min(grid, std::max<int64_t>(units, 1));
   grid = std::min(grid, max_grid);
   grid = std::max<int64_t>(grid, 1);
   void* args[] = {p};
-  cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(block), args, 0,
+  cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(l.block), args, 0,
                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  g_last = l;
+  g_last.split = p->split;
+  g_last_grid = grid;
   return COOT_OK;
 }
 
@@ -264,7 +286,7 @@ static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, u
     const int64_t fit = (int64_t)((ws_bytes - COOT_WS_PARTIALS_OFF) / (sizeof(double) * popcount(heads)));
     max_grid = std::min<int64_t>(COOT_MAX_GRID, fit);
   }
-  return launch(c, units, max_grid, l.block, &p, stream);
+  return launch(c, units, max_grid, l, &p, stream);
 }
 
 static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int dim, const coot_mat* out, void* ws,
@@ -326,8 +348,15 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     int64_t S = 1;
     if (4 * Cn < 3 * resident * warps && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
       S = std::min<int64_t>((target + Cn - 1) / Cn, (R + wt - 1) / wt);
-      S = std::min<int64_t>(S, (int64_t)(part_bytes / (sizeof(double) * std::max<int64_t>(Cn, 1))));
+      // a segment partial is a double-word pair of the compute type
+      const int64_t entry = 2 * (t.compute == COOT_F64 ? 8 : 4);
+      S = std::min<int64_t>(S, (int64_t)(part_bytes / (entry * std::max<int64_t>(Cn, 1))));
       S = std::max<int64_t>(S, 1);
+    }
+    if (l.split > 0 && Cn <= COOT_WS_MAX_COUNTERS) {
+      const int64_t entry = 2 * (t.compute == COOT_F64 ? 8 : 4);
+      S = std::min<int64_t>(l.split, (R + wt - 1) / wt);
+      S = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(part_bytes / (entry * std::max<int64_t>(Cn, 1)))));
     }
     int64_t rps = (R + S - 1) / S;
     rps = std::max<int64_t>(((rps + wt - 1) / wt) * wt, wt);
@@ -342,6 +371,7 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     const int64_t panel = 64LL * l.vec;
     const int64_t n_panels = (R + panel - 1) / panel;
     int64_t C = std::max<int64_t>(1, (2 * resident + n_panels - 1) / n_panels);
+    if (l.split > 0) C = l.split;
     C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));
     C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);
     // a chunk partial is a double-word pair of the compute type per row
@@ -353,7 +383,7 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     units = n_panels * C;
   }
   if (p.split > 1 && ws == nullptr) return fail(COOT_ERR_WORKSPACE, "split sums need a workspace");
-  return launch(c, units, INT32_MAX, l.block, &p, stream);
+  return launch(c, units, INT32_MAX, l, &p, stream);
 }
 
 }  // namespace coot
@@ -395,6 +425,38 @@ const char* coot_status_string(coot_status s) {
 }
 
 int coot_version(void) { return 100; }
+
+coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm, int64_t split) {
+  clear_error();
+  if (kind < 0 || kind > 4) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..4");
+  if (block == 0) {
+    g_override[kind] = Launch{1, 1, 0};
+    return COOT_OK;
+  }
+  if (block < 64 || block > 1024 || block % 64 != 0) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
+  if (!(vec == 0 || vec == 1 || vec == 2 || vec == 4 || vec == 8)) return fail(COOT_ERR_INVALID_ARG, "vec must be 0, 1, 2, 4 or 8");
+  if (unroll < 0 || unroll > 16) return fail(COOT_ERR_INVALID_ARG, "unroll must be 0..16");
+  if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(COOT_ERR_INVALID_ARG, "blocks_per_sm must be 0..32");
+  if (split < 0 || split > 4096) return fail(COOT_ERR_INVALID_ARG, "split must be 0..4096");
+  Launch o;
+  o.block = block;
+  o.vec = vec;
+  o.unroll = unroll;
+  o.blocks_per_sm = blocks_per_sm;
+  o.split = split;
+  g_override[kind] = o;
+  return COOT_OK;
+}
+
+coot_status coot_last_launch(int* block, int* vec, int* unroll, int64_t* grid, int64_t* split) {
+  clear_error();
+  if (block) *block = g_last.block;
+  if (vec) *vec = g_last.vec;
+  if (unroll) *unroll = g_last.unroll;
+  if (grid) *grid = g_last_grid;
+  if (split) *split = g_last.split;
+  return COOT_OK;
+}
 
 coot_status coot_workspace_size(int64_t max_rows, size_t* bytes) {
   clear_error();
@@ -618,6 +680,16 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.vec = 1;
   spec.unroll = 4;
   spec.block = 256;
+  Launch l;
+  const Launch& o = g_override[KIND_BATCHED];
+  if (o.block) {
+    spec.block = o.block;
+    if (o.unroll) spec.unroll = o.unroll;
+    l.blocks_per_sm = o.blocks_per_sm;
+  }
+  l.block = spec.block;
+  l.unroll = spec.unroll;
+  l.vec = 1;
   const Compiled* c = nullptr;
   s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;
@@ -627,7 +699,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   p.split = n_items;
   p.n_work = n_work;
   p.rows_per_split = colsum_dtype;
-  return launch(c, n_work, INT32_MAX, spec.block, &p, stream);
+  return launch(c, n_work, INT32_MAX, l, &p, stream);
 }
 
 coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws, size_t ws_bytes, void* stream) {

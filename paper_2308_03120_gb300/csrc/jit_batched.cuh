@@ -44,11 +44,13 @@ __device__ __forceinline__ void coot_load_item(const coot_batch_item_d& it, coot
 #undef COOT_LOAD_B
 }
 
-__device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, coot_i64 j, double v, bool sum64) {
+// a column sum held as a double-word pair (h, l), stored in FP64 or FP32
+__device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, coot_i64 j, COOT_REAL h, COOT_REAL l,
+                                                  bool sum64) {
   if (sum64) {
-    ((double*)it.colsum)[j * it.ld_colsum] = v;
+    ((double*)it.colsum)[j * it.ld_colsum] = coot_dw_store<3>(h, l);
   } else {
-    ((float*)it.colsum)[j * it.ld_colsum] = (float)v;
+    ((float*)it.colsum)[j * it.ld_colsum] = coot_dw_store<0>(h, l);
   }
 }
 
@@ -106,7 +108,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
           COOT_REAL vh, vl;
           coot_dw_norm(s, c, vh, vl);
           coot_dw_warp_sum(vh, vl);
-          if (lane == 0) coot_store_colsum(it, j, coot_dw_to_double(vh, vl), sum64);
+          if (lane == 0) coot_store_colsum(it, j, vh, vl, sum64);
         }
       }
     } else {
@@ -130,7 +132,9 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
           if (lane < kk) {
             COOT_REAL t = 0, tc = 0;
             for (int r = 0; r < Ri; ++r) coot_two_sum(t, tc, wbuf[warp][lane * Ri + r]);
-            coot_store_colsum(it, c0 + g0 + lane, coot_pair(t, tc), sum64);
+            COOT_REAL th, tl;
+            coot_dw_norm(t, tc, th, tl);
+            coot_store_colsum(it, c0 + g0 + lane, th, tl, sum64);
           }
           __syncwarp();
         }

@@ -48,19 +48,22 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
     coot_dw_norm(acc, accc, vh, vl);
     coot_dw_warp_sum(vh, vl);
     if (lane == 0) {
-      const double v = coot_dw_to_double(vh, vl);
       if (S == 1) {
-        ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(v);
+        ((TO*)p.out)[j * p.ld_out] = coot_dw_store<COOT_TO>(vh, vl);
       } else {
-        double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
+        // segment partials as double-word pairs: n_cols * S high parts,
+        // then n_cols * S low parts
+        COOT_REAL* part_h = (COOT_REAL*)(p.ws + COOT_WS_PARTIALS_OFF);
+        COOT_REAL* part_l = part_h + p.n_cols * S;
         coot_u32* cnt = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
-        part[j * S + s] = v;
+        part_h[j * S + s] = vh;
+        part_l[j * S + s] = vl;
         __threadfence();
         if (atomicAdd(cnt + j, 1u) == (coot_u32)(S - 1)) {
           __threadfence();
-          double t = 0.0;
-          for (coot_i64 q = 0; q < S; ++q) t += __ldcg(part + j * S + q);
-          ((TO*)p.out)[j * p.ld_out] = coot_from_double<COOT_TO>(t);
+          COOT_REAL th = 0, tl = 0;
+          for (coot_i64 q = 0; q < S; ++q) coot_dw_add(th, tl, __ldcg(part_h + j * S + q), __ldcg(part_l + j * S + q));
+          ((TO*)p.out)[j * p.ld_out] = coot_dw_store<COOT_TO>(th, tl);
           cnt[j] = 0u;
         }
       }

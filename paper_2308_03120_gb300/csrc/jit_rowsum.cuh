@@ -93,7 +93,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       if (ty == 0) {
 #pragma unroll
         for (int v = 0; v < COOT_VEC; ++v)
-          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(coot_dw_to_double(th[v], tl[v]));
+          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_dw_store<COOT_TO>(th[v], tl[v]);
       }
       __syncthreads();  // red is rewritten by the next unit
       continue;
@@ -136,7 +136,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
           COOT_REAL wh = red_h[0][tx * COOT_VEC + v], wl = red_l[0][tx * COOT_VEC + v];
 #pragma unroll
           for (int g = 1; g < COOT_CG; ++g) coot_dw_add(wh, wl, red_h[g][tx * COOT_VEC + v], red_l[g][tx * COOT_VEC + v]);
-          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_from_double<COOT_TO>(coot_dw_to_double(wh, wl));
+          if (i0 + v < p.n_rows) ((TO*)p.out)[i0 + v] = coot_dw_store<COOT_TO>(wh, wl);
         }
       }
       if (threadIdx.x == 0) cnt[panel] = 0u;

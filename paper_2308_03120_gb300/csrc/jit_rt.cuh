@@ -379,6 +379,18 @@ __device__ __forceinline__ double coot_dw_to_double(COOT_REAL h, COOT_REAL l) {
   return isfinite(hd) ? hd + (double)l : hd;
 }
 
+// A double-word sum stored in storage type S: FP64 storage gets h + l in
+// FP64; any other type gets h + l rounded in the compute type (one rounding
+// of the normalised pair, no FP64 instruction), then converted.
+template <int S>
+__device__ __forceinline__ typename coot_st<S>::T coot_dw_store(COOT_REAL h, COOT_REAL l) {
+  if constexpr (S == 3) {
+    return coot_dw_to_double(h, l);
+  } else {
+    return coot_from_real<S>(isfinite(h) ? h + l : h);
+  }
+}
+
 // the pair as one FP64 value; once the sum is infinite or NaN the
 // compensation carries inf - inf and is dropped
 __device__ __forceinline__ double coot_pair(COOT_REAL s, COOT_REAL c) {

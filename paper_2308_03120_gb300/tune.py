@@ -1,0 +1,128 @@
+"""Exhaustive launch-shape tuning.
+
+For one call (a closure that issues coot calls on the current stream) and
+one kernel kind, every launch shape of a grid is set with
+coot_set_launch_config, compiled on first use, and timed with CUDA events
+(median over repetitions, inputs larger than L2 or an L2 flush between
+repetitions when asked).  The fastest shape is the tuner's answer; the
+whole table is the data the learned launch-shape model trains on.
+
+    python -m paper_2308_03120_gb300.tune            # the matrix workload's four calls
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import statistics
+import sys
+
+from . import KIND_BATCHED, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSUM  # noqa: F401
+
+GRIDS = {
+    KIND_MAP: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
+    KIND_REDUCE: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
+    KIND_COLSUM: dict(block=[128, 256, 512], vec=[0], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0, 1, 2, 4]),
+    KIND_ROWSUM: dict(block=[64, 128, 256, 512], vec=[0], unroll=[2, 4, 8, 16], blocks_per_sm=[0],
+                      split=[0, 8, 16, 32, 64]),
+    KIND_BATCHED: dict(block=[128, 256, 512], vec=[0], unroll=[1, 2, 4, 8], blocks_per_sm=[0, 2, 4], split=[0]),
+}
+
+
+def configs(kind: int, grid: dict | None = None):
+    g = grid or GRIDS[kind]
+    keys = ["block", "vec", "unroll", "blocks_per_sm", "split"]
+    for vals in itertools.product(*(g[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+def time_call(fn, reps: int = 10, warmup: int = 2, flush=None) -> float:
+    """Median device time of fn() in milliseconds (CUDA events on the
+    current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def sweep(fn, kind: int, grid: dict | None = None, reps: int = 10, flush=None):
+    """Time fn under every launch shape of the grid for `kind`; returns
+    [(ms, config, launch actually used)] sorted by time.  The built-in
+    choice is timed too (config None)."""
+    import paper_2308_03120_gb300 as coot
+    out = []
+    try:
+        coot.coot_set_launch_config(kind, 0)
+        ms = time_call(fn, reps, flush=flush)
+        out.append((ms, None, coot.coot_last_launch()))
+        for cfg in configs(kind, grid):
+            coot.coot_set_launch_config(kind, **cfg)
+            ms = time_call(fn, reps, flush=flush)
+            out.append((ms, cfg, coot.coot_last_launch()))
+    finally:
+        coot.coot_set_launch_config(kind, 0)
+    return sorted(out, key=lambda r: r[0])
+
+
+def _matrix_workload(n: int = 8192):
+    import torch
+
+    import paper_2308_03120_gb300 as coot
+    import synth
+    seed = synth.BASE_SEED + 1
+    dev = [torch.from_numpy(synth.uniform_f32(seed + k, n * n, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0))
+           .cuda() for k in range(4)]
+    mats = [coot.Mat(t, n, n, n) for t in dev]
+    out1 = torch.empty(n * n, device="cuda")
+    out2 = torch.empty(n * n, device="cuda")
+    col = torch.empty(n, device="cuda")
+    row = torch.empty(n, device="cuda")
+    res = torch.empty(4, dtype=torch.float64, device="cuda")
+    ws = coot.Workspace(n)
+    t_expr = coot.serialize(synth.MAT_EXPR)
+    t_chain = coot.serialize(synth.MAT_CHAIN)
+    leaf = coot.serialize(synth.LEAF0)
+    heads = coot.HEAD_SUM | coot.HEAD_NORM2 | coot.HEAD_MIN | coot.HEAD_MAX
+    O1 = coot.Mat(out1, n, n, n)
+    return {
+        "expr_reduce": (KIND_MAP, 5 * n * n * 4,
+                        lambda: coot.coot_expr_reduce(t_expr, mats, heads, out=O1, out_dev=res, ws=ws)),
+        "expr_eval": (KIND_MAP, 5 * n * n * 4, lambda: coot.coot_expr_eval(t_chain, mats, coot.Mat(out2, n, n, n))),
+        "sum_dim0": (KIND_COLSUM, n * n * 4, lambda: coot.coot_sum_dim(leaf, [O1], 0, coot.Mat(col, 1, n, 1), ws=ws)),
+        "sum_dim1": (KIND_ROWSUM, n * n * 4, lambda: coot.coot_sum_dim(leaf, [O1], 1, coot.Mat(row, n, 1, n), ws=ws)),
+    }
+
+
+def main(argv=None):
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build
+    build.build()
+    coot.coot_init(0)
+    calls = _matrix_workload()
+    report = {}
+    for name, (kind, nbytes, fn) in calls.items():
+        fn()
+        res = sweep(fn, kind, reps=8)
+        base = next(r for r in res if r[1] is None)
+        best = res[0]
+        report[name] = {"builtin_ms": round(base[0], 4), "builtin_gbs": round(nbytes / base[0] / 1e6, 1),
+                        "builtin": base[2], "best_ms": round(best[0], 4), "best_gbs": round(nbytes / best[0] / 1e6, 1),
+                        "best": best[1], "best_launch": best[2],
+                        "top5": [(round(r[0], 4), r[1]) for r in res[:5]]}
+        print(name, json.dumps(report[name]), flush=True)
+    return report
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -132,6 +132,48 @@ def test_fp64_compute():
     _eval_case(synth.MAT_CHAIN, specs, 13, out_dtype="f64", compute="f64")
 
 
+@pytest.mark.parametrize("cfg", [dict(block=64, vec=1, unroll=1), dict(block=512, vec=2, unroll=8),
+                                 dict(block=128, vec=0, unroll=16, blocks_per_sm=1),
+                                 dict(block=1024, vec=4, unroll=3, split=3)])
+def test_launch_shapes_keep_results(cfg):
+    """Every kernel kind under launch shapes other than the built-in one:
+    element values are identical, sums agree with the oracle."""
+    r, c = 1537, 129
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(synth.MAT_EXPR, specs, 23)
+    ref = Out(r, c)
+    coot.coot_expr_eval(tree, dev, ref.mat)
+    t, e = _terms(tree, ins)
+    v, bound, _ = O.error_bound(tree, ins)
+    try:
+        for kind in (coot.KIND_MAP, coot.KIND_REDUCE, coot.KIND_COLSUM, coot.KIND_ROWSUM):
+            coot.coot_set_launch_config(kind, **cfg)
+        out = Out(r, c)
+        coot.coot_expr_eval(tree, dev, out.mat)
+        s = coot.coot_accu(tree, dev).item()
+        o0, o1 = Out(1, c, "f64"), Out(r, 1, "f64")
+        coot.coot_sum_dim(tree, dev, 0, o0.mat)
+        coot.coot_sum_dim(tree, dev, 1, o1.mat)
+        last = coot.coot_last_launch()
+        torch.cuda.synchronize()
+    finally:
+        for kind in range(5):
+            coot.coot_set_launch_config(kind, 0)
+    assert last["block"] == cfg["block"]
+    out.check()
+    check_elementwise(tree, ins, out.host())
+    assert_sum_close(s, O.accu(tree, ins), t, e, "accu")
+    for dim, o in ((0, o0), (1, o1)):
+        got = O.logical(o.host()).ravel()
+        want = O.sum_dim(tree, ins, dim)
+        terms = v if dim == 0 else v.T
+        errs = bound if dim == 0 else bound.T
+        s_abs = np.sum(np.abs(terms), axis=0)
+        tol = 1e-6 * np.abs(want) + np.where(np.abs(want) < 1e-3 * s_abs, 1e-9 * s_abs, 0.0)
+        tol += 6.0 * np.sqrt(np.sum(errs * errs, axis=0))
+        assert np.all(np.abs(got - want) <= tol), dim
+
+
 def test_fp64_compute_reductions():
     """FP64 trees: full reductions and sums along both dims (the per-thread
     pairs and their combination run in FP64 double-word arithmetic)."""
