@@ -174,12 +174,18 @@ static thread_local int64_t g_last_grid = 0;
 static Launch heuristic(int kind, int n_in, const View& v) {
   Launch l;
   const Launch& o = g_override[kind];
+  // built-in choices, from exhaustive sweeps on GB300 (see the tuning
+  // module): many bytes in flight per thread beat occupancy for these
+  // streaming kernels
   l.vec = pick_vec(v);
   l.block = 256;
   if (kind == KIND_ROWSUM) {
+    l.block = 512;
     l.unroll = n_in >= 3 ? 4 : 8;
+  } else if (kind == KIND_COLSUM) {
+    l.unroll = 4;
   } else {
-    l.unroll = std::max(1, std::min(4, 8 / std::max(1, n_in)));
+    l.unroll = n_in >= 3 ? 4 : 8;
   }
   if (o.block) {
     l.block = o.block;
@@ -340,13 +346,13 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   const size_t part_bytes = ws ? (ws_bytes > COOT_WS_PARTIALS_OFF ? ws_bytes - COOT_WS_PARTIALS_OFF : 0) : 0;
   int64_t units;  // blocks' worth of work
   if (dim == 0) {
-    // a warp per (column, segment); split the columns into segments until
-    // there are about three units per resident warp
+    // a warp per (column, segment); with fewer columns than about 1.5 per
+    // resident warp, split the columns into segments up to that count
     const int64_t warps = l.block / 32;
     const int64_t wt = 32LL * l.vec * l.unroll;  // rows per warp tile
-    const int64_t target = 3 * resident * warps;
+    const int64_t target = 3 * resident * warps / 2;
     int64_t S = 1;
-    if (4 * Cn < 3 * resident * warps && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
+    if (Cn < target && R > wt && Cn <= COOT_WS_MAX_COUNTERS) {
       S = std::min<int64_t>((target + Cn - 1) / Cn, (R + wt - 1) / wt);
       // a segment partial is a double-word pair of the compute type
       const int64_t entry = 2 * (t.compute == COOT_F64 ? 8 : 4);
@@ -365,12 +371,13 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
     p.rows_per_split = rps;
     units = (Cn * S + warps - 1) / warps;
   } else {
-    // panels of 64 * vec rows; chunks of columns until about two blocks
-    // per resident block slot
+    // panels of 64 * vec rows; chunks of columns until there are about 1.5
+    // units per SM (large units: few partials, little per-unit overhead)
     const int64_t groups = std::max(1, l.block / 64);
     const int64_t panel = 64LL * l.vec;
     const int64_t n_panels = (R + panel - 1) / panel;
-    int64_t C = std::max<int64_t>(1, (2 * resident + n_panels - 1) / n_panels);
+    const int64_t target = 3 * (int64_t)d.sm_count / 2;
+    int64_t C = std::max<int64_t>(1, (target + n_panels - 1) / n_panels);
     if (l.split > 0) C = l.split;
     C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));
     C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);

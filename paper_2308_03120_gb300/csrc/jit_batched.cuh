@@ -17,7 +17,7 @@ struct coot_batch_item_d {
 };
 
 // One unit of the work list: columns [col0, col0 + n_cols) of one matrix,
-// handled by one block; units hold a few thousand elements, so the cost of
+// handled by one block; units hold up to about 8K elements, so the cost of
 // reading the unit and its matrix descriptor is spread over many loads.
 struct coot_work_d {
   int item;
@@ -27,6 +27,9 @@ struct coot_work_d {
 };
 
 #if COOT_KIND == 4
+// staged element values of one unit (32 KB)
+#define COOT_STAGE (32768 / (int)sizeof(COOT_REAL))
+
 __device__ __forceinline__ void coot_load_item(const coot_batch_item_d& it, coot_i64 j, coot_i64 row,
                                                COOT_REAL (&x)[4]) {
 #define COOT_LOAD_B(I)                                                                    \
@@ -44,6 +47,23 @@ __device__ __forceinline__ void coot_load_item(const coot_batch_item_d& it, coot
 #undef COOT_LOAD_B
 }
 
+// element e of the flat (dense) range starting at element b
+__device__ __forceinline__ void coot_load_flat(const coot_batch_item_d& it, coot_i64 e, COOT_REAL (&x)[4]) {
+#define COOT_LOAD_F(I)                                                                    \
+  if constexpr (I < COOT_NIN) {                                                           \
+    constexpr int S = coot_in_code<I>::S;                                                 \
+    typedef typename coot_st<S>::T T;                                                     \
+    x[I] = coot_sload<S>((const T*)it.in[I] + e);                                         \
+  } else {                                                                                \
+    x[I] = (COOT_REAL)0;                                                                  \
+  }
+  COOT_LOAD_F(0)
+  COOT_LOAD_F(1)
+  COOT_LOAD_F(2)
+  COOT_LOAD_F(3)
+#undef COOT_LOAD_F
+}
+
 // a column sum held as a double-word pair (h, l), stored in FP64 or FP32
 __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, coot_i64 j, COOT_REAL h, COOT_REAL l,
                                                   bool sum64) {
@@ -57,13 +77,17 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // p.plan: items (p.split of them) followed by the work list (p.n_work units).
 // COOT_TO is the storage code of the element-wise outputs; the column sums
 // are stored in the storage code given by p.rows_per_split (0 FP32, 3 FP64).
-// Columns of at least 32 rows: warp w of the block takes columns w, w +
-// warps, ... of the unit, lanes stride down the rows, COOT_UNROLL rows per
-// lane in flight, then a warp-shuffle sum.  Shorter columns: floor(32 /
-// n_rows) columns side by side in one warp, summed through shared memory
-// in row order.
+//
+// Dense units (every operand's ld equals n_rows, so the unit's columns are
+// one contiguous run) that fit the stage: every thread streams the run
+// flat, COOT_UNROLL elements per input in flight, writes the values and
+// keeps them in shared memory; the column sums are then taken from shared
+// memory (a warp per column with a double-word shuffle sum for columns of
+// at least 32 rows, a thread per column below that), each in a fixed order.
+// Other units: warp w of the block takes columns w, w + warps, ...; lanes
+// stride down the rows.
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
-  __shared__ COOT_REAL wbuf[COOT_WARPS][32];
+  __shared__ COOT_REAL stage[COOT_STAGE];
   __shared__ coot_batch_item_d sit;
   __shared__ coot_work_d swk;
   typedef typename coot_st<COOT_TO>::T TO;
@@ -72,7 +96,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool sum64 = p.rows_per_split == 3;
   for (coot_i64 w = blockIdx.x; w < p.n_work; w += gridDim.x) {
-    __syncthreads();  // the previous unit is done with sit / swk
+    __syncthreads();  // the previous unit is done with sit, swk and stage
     if (threadIdx.x == 0) {
       swk = work[w];
       sit = items[swk.item];
@@ -80,64 +104,90 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
     __syncthreads();
     // a register copy: read from shared memory, the pointers would be
     // reloaded after every store and serialise the loads
-    const coot_batch_item_d it = sit;
+    coot_batch_item_d it = sit;
     const coot_i64 R = it.n_rows;
     const coot_i64 c0 = swk.col0, nc = swk.n_cols;
-    if (R >= 32) {
-      for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
-        const coot_i64 j = c0 + cj;
-        COOT_REAL s = 0, c = 0;
-        for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
-          COOT_REAL xv[COOT_UNROLL][4];
+    bool dense = (it.out == nullptr || it.ld_out == R);
 #pragma unroll
-          for (int q = 0; q < COOT_UNROLL; ++q) {
-            const coot_i64 r = r0 + 32 * q + lane;
-            if (r < R) coot_load_item(it, j, r, xv[q]);
-          }
+    for (int k = 0; k < COOT_NIN; ++k) dense = dense && it.ld_in[k] == R;
+    const coot_i64 n = nc * R;
+    if (dense && n <= COOT_STAGE) {
+      // the unit's run starts at element b of every operand
+      const coot_i64 b = c0 * R;
+#define COOT_SHIFT(I)                                                                                   \
+  if constexpr (I < COOT_NIN) it.in[I] = (const typename coot_st<coot_in_code<I>::S>::T*)it.in[I] + b;
+      COOT_SHIFT(0)
+      COOT_SHIFT(1)
+      COOT_SHIFT(2)
+      COOT_SHIFT(3)
+#undef COOT_SHIFT
+      TO* out = it.out ? (TO*)it.out + b : (TO*)nullptr;
+      for (coot_i64 e0 = 0; e0 < n; e0 += (coot_i64)COOT_BLOCK * COOT_UNROLL) {
+        COOT_REAL xv[COOT_UNROLL][4];
 #pragma unroll
-          for (int q = 0; q < COOT_UNROLL; ++q) {
-            const coot_i64 r = r0 + 32 * q + lane;
-            if (r < R) {
-              const COOT_REAL y = coot_f(xv[q]);
-              if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
-              coot_two_sum(s, c, y);
-            }
-          }
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 e = e0 + (coot_i64)q * COOT_BLOCK + threadIdx.x;
+          if (e < n) coot_load_flat(it, e, xv[q]);
         }
-        if (it.colsum) {
-          COOT_REAL vh, vl;
-          coot_dw_norm(s, c, vh, vl);
-          coot_dw_warp_sum(vh, vl);
-          if (lane == 0) coot_store_colsum(it, j, vh, vl, sum64);
+#pragma unroll
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 e = e0 + (coot_i64)q * COOT_BLOCK + threadIdx.x;
+          if (e < n) {
+            const COOT_REAL y = coot_f(xv[q]);
+            if (out) out[e] = coot_from_real<COOT_TO>(y);
+            stage[e] = y;
+          }
         }
       }
-    } else {
-      // k short columns side by side per warp: lane -> (column, row)
-      const int Ri = (int)R;
-      const int k = Ri > 0 ? 32 / Ri : 32;
-      for (coot_i64 g0 = (coot_i64)warp * k; g0 < nc; g0 += (coot_i64)COOT_WARPS * k) {
-        const int kk = (int)min((coot_i64)k, nc - g0);
-        COOT_REAL y = 0;
-        if (lane < kk * Ri) {
-          const int cl = lane / Ri, r = lane - cl * Ri;
-          const coot_i64 j = c0 + g0 + cl;
-          COOT_REAL x[4];
-          coot_load_item(it, j, r, x);
-          y = coot_f(x);
-          if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
-        }
-        if (it.colsum) {
-          wbuf[warp][lane] = y;
-          __syncwarp();
-          if (lane < kk) {
-            COOT_REAL t = 0, tc = 0;
-            for (int r = 0; r < Ri; ++r) coot_two_sum(t, tc, wbuf[warp][lane * Ri + r]);
-            COOT_REAL th, tl;
-            coot_dw_norm(t, tc, th, tl);
-            coot_store_colsum(it, c0 + g0 + lane, th, tl, sum64);
+      if (it.colsum) {
+        __syncthreads();
+        if (R >= 32) {
+          for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
+            COOT_REAL s = 0, c = 0;
+            for (coot_i64 r = lane; r < R; r += 32) coot_two_sum(s, c, stage[cj * R + r]);
+            COOT_REAL vh, vl;
+            coot_dw_norm(s, c, vh, vl);
+            coot_dw_warp_sum(vh, vl);
+            if (lane == 0) coot_store_colsum(it, c0 + cj, vh, vl, sum64);
           }
-          __syncwarp();
+        } else {
+          for (coot_i64 cj = threadIdx.x; cj < nc; cj += COOT_BLOCK) {
+            COOT_REAL s = 0, c = 0;
+            for (coot_i64 r = 0; r < R; ++r) coot_two_sum(s, c, stage[cj * R + r]);
+            COOT_REAL vh, vl;
+            coot_dw_norm(s, c, vh, vl);
+            coot_store_colsum(it, c0 + cj, vh, vl, sum64);
+          }
         }
+      }
+      continue;
+    }
+    // strided operands or a unit larger than the stage: a warp per column
+    for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
+      const coot_i64 j = c0 + cj;
+      COOT_REAL s = 0, c = 0;
+      for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
+        COOT_REAL xv[COOT_UNROLL][4];
+#pragma unroll
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 r = r0 + 32 * q + lane;
+          if (r < R) coot_load_item(it, j, r, xv[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < COOT_UNROLL; ++q) {
+          const coot_i64 r = r0 + 32 * q + lane;
+          if (r < R) {
+            const COOT_REAL y = coot_f(xv[q]);
+            if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
+            coot_two_sum(s, c, y);
+          }
+        }
+      }
+      if (it.colsum) {
+        COOT_REAL vh, vl;
+        coot_dw_norm(s, c, vh, vl);
+        coot_dw_warp_sum(vh, vl);
+        if (lane == 0) coot_store_colsum(it, j, vh, vl, sum64);
       }
     }
   }
