@@ -613,7 +613,12 @@ static_assert(sizeof(WorkUnit) == 16, "work unit layout");
 static int64_t cols_per_unit(int64_t n_rows) {
   const int64_t target = 8192;
   if (n_rows <= 0) return target;
-  return std::max<int64_t>(1, target / n_rows);
+  int64_t k = std::max<int64_t>(1, target / n_rows);
+  // keep col0 * n_rows a multiple of 4 elements, so that a unit of a
+  // 16-byte aligned matrix starts 16-byte aligned (vector accesses)
+  const int64_t m = n_rows % 4 == 0 ? 1 : (n_rows % 2 == 0 ? 2 : 4);
+  if (k >= m) k -= k % m;
+  return k;
 }
 
 coot_status coot_batch_plan_size(const coot_batch_item* items, int n_items, size_t* bytes, int64_t* n_work) {
@@ -684,8 +689,8 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   for (int i = 0; i < t.n_inputs; ++i) spec.in_dtype[i] = in_dtypes[i];
   spec.out_dtype = out_dtype;
   spec.store = true;
-  spec.vec = 1;
-  spec.unroll = 4;
+  spec.vec = 4;
+  spec.unroll = 2;
   spec.block = 256;
   Launch l;
   const Launch& o = g_override[KIND_BATCHED];
@@ -696,7 +701,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   }
   l.block = spec.block;
   l.unroll = spec.unroll;
-  l.vec = 1;
+  l.vec = spec.vec;
   const Compiled* c = nullptr;
   s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;

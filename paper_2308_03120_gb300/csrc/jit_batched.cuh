@@ -64,6 +64,30 @@ __device__ __forceinline__ void coot_load_flat(const coot_batch_item_d& it, coot
 #undef COOT_LOAD_F
 }
 
+// COOT_VEC consecutive elements of every input from element e of the
+// (shifted, dense) run; e is a multiple of COOT_VEC and the run is aligned
+__device__ __forceinline__ void coot_load_flat_vec(const coot_batch_item_d& it, int e,
+                                                   COOT_REAL (&x)[4][COOT_VEC]) {
+#define COOT_LOAD_V(I)                                                                    \
+  if constexpr (I < COOT_NIN) {                                                           \
+    constexpr int S = coot_in_code<I>::S;                                                 \
+    typedef typename coot_st<S>::T T;                                                     \
+    coot_vload<S, COOT_VEC>((const T*)it.in[I] + e, x[I]);                                \
+  } else {                                                                                \
+    _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = (COOT_REAL)0;          \
+  }
+  COOT_LOAD_V(0)
+  COOT_LOAD_V(1)
+  COOT_LOAD_V(2)
+  COOT_LOAD_V(3)
+#undef COOT_LOAD_V
+}
+
+template <int S>
+__device__ __forceinline__ bool coot_aligned16(const void* p) {
+  return ((unsigned long long)p & 15ull) == 0;
+}
+
 // a column sum held as a double-word pair (h, l), stored in FP64 or FP32
 __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, coot_i64 j, COOT_REAL h, COOT_REAL l,
                                                   bool sum64) {
@@ -86,7 +110,10 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // at least 32 rows, a thread per column below that), each in a fixed order.
 // Other units: warp w of the block takes columns w, w + warps, ...; lanes
 // stride down the rows.
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_params p) {
+// at least 1024 threads resident per SM: the per-unit barriers leave
+// latency that only other blocks can hide
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK < 1024 ? 1024 / COOT_BLOCK : 1))
+    COOT_ENTRY(const __grid_constant__ coot_params p) {
   __shared__ COOT_REAL stage[COOT_STAGE];
   __shared__ coot_batch_item_d sit;
   __shared__ coot_work_d swk;
@@ -122,38 +149,58 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
       COOT_SHIFT(3)
 #undef COOT_SHIFT
       TO* out = it.out ? (TO*)it.out + b : (TO*)nullptr;
-      for (coot_i64 e0 = 0; e0 < n; e0 += (coot_i64)COOT_BLOCK * COOT_UNROLL) {
-        COOT_REAL xv[COOT_UNROLL][4];
+      const int ni = (int)n;
+      // vectors of COOT_VEC elements when every operand's run is 16-byte
+      // aligned (the plan cuts units so that it usually is)
+      bool va = out == nullptr || coot_aligned16<0>(out);
+#pragma unroll
+      for (int k = 0; k < COOT_NIN; ++k) va = va && coot_aligned16<0>(it.in[k]);
+      const int nv = va ? ni / COOT_VEC : 0;
+      for (int v0 = 0; v0 < nv; v0 += COOT_BLOCK * COOT_UNROLL) {
+        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
 #pragma unroll
         for (int q = 0; q < COOT_UNROLL; ++q) {
-          const coot_i64 e = e0 + (coot_i64)q * COOT_BLOCK + threadIdx.x;
-          if (e < n) coot_load_flat(it, e, xv[q]);
+          const int v = v0 + q * COOT_BLOCK + (int)threadIdx.x;
+          if (v < nv) coot_load_flat_vec(it, v * COOT_VEC, xv[q]);
         }
 #pragma unroll
         for (int q = 0; q < COOT_UNROLL; ++q) {
-          const coot_i64 e = e0 + (coot_i64)q * COOT_BLOCK + threadIdx.x;
-          if (e < n) {
-            const COOT_REAL y = coot_f(xv[q]);
-            if (out) out[e] = coot_from_real<COOT_TO>(y);
-            stage[e] = y;
+          const int v = v0 + q * COOT_BLOCK + (int)threadIdx.x;
+          if (v < nv) {
+            COOT_REAL y[COOT_VEC];
+#pragma unroll
+            for (int k = 0; k < COOT_VEC; ++k) {
+              const COOT_REAL x[4] = {xv[q][0][k], xv[q][1][k], xv[q][2][k], xv[q][3][k]};
+              y[k] = coot_f(x);
+              stage[v * COOT_VEC + k] = y[k];
+            }
+            if (out) coot_vstore<COOT_TO, COOT_VEC>(out + v * COOT_VEC, y);
           }
         }
       }
+      for (int e = nv * COOT_VEC + (int)threadIdx.x; e < ni; e += COOT_BLOCK) {
+        COOT_REAL x[4];
+        coot_load_flat(it, e, x);
+        const COOT_REAL y = coot_f(x);
+        if (out) out[e] = coot_from_real<COOT_TO>(y);
+        stage[e] = y;
+      }
       if (it.colsum) {
         __syncthreads();
-        if (R >= 32) {
-          for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
+        const int Ri = (int)R, nci = (int)nc;
+        if (Ri >= 32) {
+          for (int cj = warp; cj < nci; cj += COOT_WARPS) {
             COOT_REAL s = 0, c = 0;
-            for (coot_i64 r = lane; r < R; r += 32) coot_two_sum(s, c, stage[cj * R + r]);
+            for (int r = lane; r < Ri; r += 32) coot_two_sum(s, c, stage[cj * Ri + r]);
             COOT_REAL vh, vl;
             coot_dw_norm(s, c, vh, vl);
             coot_dw_warp_sum(vh, vl);
             if (lane == 0) coot_store_colsum(it, c0 + cj, vh, vl, sum64);
           }
         } else {
-          for (coot_i64 cj = threadIdx.x; cj < nc; cj += COOT_BLOCK) {
+          for (int cj = threadIdx.x; cj < nci; cj += COOT_BLOCK) {
             COOT_REAL s = 0, c = 0;
-            for (coot_i64 r = 0; r < R; ++r) coot_two_sum(s, c, stage[cj * R + r]);
+            for (int r = 0; r < Ri; ++r) coot_two_sum(s, c, stage[cj * Ri + r]);
             COOT_REAL vh, vl;
             coot_dw_norm(s, c, vh, vl);
             coot_store_colsum(it, c0 + cj, vh, vl, sum64);

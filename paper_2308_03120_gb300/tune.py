@@ -104,12 +104,40 @@ def _matrix_workload(n: int = 8192):
     }
 
 
+def _batched_workload(nmat: int = 4096):
+    import numpy as np
+    import torch
+
+    import paper_2308_03120_gb300 as coot
+    import synth
+    rows = synth.loguniform_int(synth.BASE_SEED + 3, nmat, 1, 512)
+    cols = synth.loguniform_int(synth.BASE_SEED + 4, nmat, 1, 512)
+    sizes = (rows * cols).astype(np.int64)
+    offs = np.zeros(nmat + 1, dtype=np.int64)
+    offs[1:] = np.cumsum((sizes + 3) // 4 * 4)
+    coff = np.zeros(nmat + 1, dtype=np.int64)
+    coff[1:] = np.cumsum((cols + 3) // 4 * 4)
+    bufs = [torch.from_numpy(synth.uniform_f32(synth.BASE_SEED + 10 + k, int(offs[-1]))).cuda() for k in range(3)]
+    out = torch.empty(int(offs[-1]), device="cuda")
+    csum = torch.empty(int(coff[-1]), device="cuda")
+    items = []
+    for m in range(nmat):
+        r, c, o = int(rows[m]), int(cols[m]), int(offs[m])
+        items.append(coot.batch_item([coot.Mat(b, r, c, r, o) for b in bufs], coot.Mat(out, r, c, r, o),
+                                     coot.Mat(csum, 1, c, 1, int(coff[m]))))
+    plan, n_items, n_work = coot.coot_batch_plan(items, 3)
+    tree = coot.serialize(synth.BATCH_EXPR)
+    nbytes = int(sizes.sum()) * 16 + int(cols.sum()) * 4
+    return {"batched": (KIND_BATCHED, nbytes,
+                        lambda: coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work))}
+
+
 def main(argv=None):
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build
     build.build()
     coot.coot_init(0)
-    calls = _matrix_workload()
+    calls = _batched_workload() if argv and argv[0] == "batched" else _matrix_workload()
     report = {}
     for name, (kind, nbytes, fn) in calls.items():
         fn()
