@@ -428,3 +428,34 @@ def test_unfused_baseline_matches(sexpr):
     torch.cuda.synchronize()
     out.check()
     check_elementwise(tree, ins[:n_in], out.host())
+
+
+def test_shard_local_results_on_gpu():
+    """The per-rank reductions of the sharded path (shard.gpu_local) through
+    the combine, as a one-rank gloo group, against the oracle."""
+    import os
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2308_03120_gb300.shard import combine, gpu_local
+    r, c = 777, 55
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _red_inputs(synth.MAT_EXPR, specs, 29)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        res = combine(gpu_local(tree, dev), c)
+    finally:
+        dist.destroy_process_group()
+    t, e = _terms(tree, ins)
+    assert_sum_close(res["accu"], O.accu(tree, ins), t, e, "accu")
+    assert abs(res["norm_fro"] - O.norm(tree, ins, "fro")) <= 1e-6 * O.norm(tree, ins, "fro")
+    lo, hi = O.minmax(tree, ins)
+    assert abs(res["min"] - lo) <= 2 * float(e.max()) and abs(res["max"] - hi) <= 2 * float(e.max())
+    assert np.allclose(res["sum_dim0"], O.sum_dim(tree, ins, 0), rtol=1e-6, atol=1e-5)
+    assert np.allclose(res["sum_dim1"], O.sum_dim(tree, ins, 1), rtol=1e-6, atol=1e-5)
