@@ -203,6 +203,15 @@ coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
 coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm,
                                    int64_t split);
 
+/* Compile and load (without launching) the kernel a call of this kind
+ * would use with exactly this launch shape (vec 1/2/4/8, unroll 1..16):
+ * first-use compilation moves out of timed regions and graph captures.
+ * dtypes: host array of the tree's input storage types; out_dtype: -1 when
+ * nothing element-wise is stored.  Thread-safe; threads compile in
+ * parallel.  Needs coot_init. */
+coot_status coot_prepare(const uint8_t* tree, size_t tree_len, int kind, const int32_t* dtypes,
+                         int out_dtype, unsigned heads, int block, int vec, int unroll);
+
 /* Launch shape of the last kernel launched by a coot call on this thread
  * (any out pointer may be NULL).  Host-only. */
 coot_status coot_last_launch(int* block, int* vec, int* unroll, int64_t* grid, int64_t* split);
@@ -332,6 +341,71 @@ coot_status coot_batch_plan_build(const coot_batch_item* items, int n_items, int
 coot_status coot_expr_eval_batched(const uint8_t* tree, size_t tree_len, const int32_t* in_dtypes,
                                    int32_t out_dtype, int32_t colsum_dtype, const void* plan_dev,
                                    int n_items, int64_t n_work, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned launch shapes (not in the paper).  A cost model predicts the
+ * log of a kernel's time from features of the call and of a candidate
+ * launch shape; with the learned policy on, each call takes the candidate
+ * with the lowest prediction.  The model is a 2-layer MLP trained on
+ * timings the library measures itself, on the GPU, by the functions below.
+ *
+ * Parameters: one FP32 array, W1 (d x h, row-major: W1[i * h + j] maps
+ * input i to hidden unit j), b1 (h), W2 (h x h), b2 (h), w3 (h), b3 (1);
+ * n = d h + h + h h + 3 h + 1.  Forward: h1 = relu(x W1 + b1), h2 =
+ * relu(h1 W2 + b2), y = h2 . w3 + b3.
+ * ---------------------------------------------------------------------- */
+
+#define COOT_MODEL_FEATURES 21
+#define COOT_MODEL_HIDDEN 64
+#define COOT_POLICY_BUILTIN 0
+#define COOT_POLICY_LEARNED 1
+
+/* y[b] for the batch x (batch x d, row-major), all device pointers; act
+ * receives h1 then h2 (2 * batch * h floats, device) for the gradient. */
+coot_status coot_mlp_forward(const float* params, int d, int h, const float* x, int batch, float* y,
+                             float* act, void* stream);
+
+/* loss[0] = mean (y - t)^2 and grad = d loss / d params (packed like params)
+ * for the batch (x, t) whose forward (y, act) was just computed; work:
+ * device scratch of batch * (2 h + 1) floats.  Sums over the batch run in
+ * a fixed order: the result is reproducible. */
+coot_status coot_mlp_loss_grad(const float* params, int d, int h, const float* x, const float* t,
+                               int batch, const float* y, const float* act, float* grad, float* loss,
+                               float* work, void* stream);
+
+/* One Adam step (step >= 1 counts the steps for the bias correction):
+ * m, v are the caller's zero-initialised moment arrays. */
+coot_status coot_mlp_adam(float* params, const float* grad, float* m, float* v, int n, int step,
+                          float lr, float beta1, float beta2, float eps, void* stream);
+
+/* The COOT_MODEL_FEATURES features of a call and a candidate launch shape
+ * (the model's input; host-only).  kind as coot_set_launch_config (0..3);
+ * dtypes: host array of the tree's n_inputs storage types; out_dtype: -1
+ * when nothing element-wise is stored; heads: COOT_HEAD_* mask; dense: 1
+ * when every operand has ld == n_rows. */
+coot_status coot_call_features(const uint8_t* tree, size_t tree_len, int kind, const int32_t* dtypes,
+                               int out_dtype, unsigned heads, int64_t n_rows, int64_t n_cols,
+                               int dense, int block, int vec, int unroll, int64_t split,
+                               float* features);
+
+/* Load cost-model parameters (d = COOT_MODEL_FEATURES, h =
+ * COOT_MODEL_HIDDEN; host array of n floats, copied). */
+coot_status coot_model_load(const float* params, size_t n);
+
+/* Predicted log time of feature rows (host arrays; host computation,
+ * FP64 internally). */
+coot_status coot_model_predict(const float* features, int n_rows, float* out);
+
+/* The candidate launch shapes the learned policy chooses among for a kind
+ * (0..3): *n receives their count; out (may be NULL) receives up to max of
+ * them as {block, vec, unroll, split} int32 quadruples (vec 0: widest
+ * aligned; split 0: chosen from the shape).  Host-only. */
+coot_status coot_launch_candidates(int kind, int32_t* out, int max, int* n);
+
+/* COOT_POLICY_BUILTIN (default) or COOT_POLICY_LEARNED (needs a loaded
+ * model; kinds 0-3).  A launch shape set with coot_set_launch_config still
+ * wins over either. */
+coot_status coot_set_policy(int policy);
 
 /* ------------------------------------------------------------------------
  * Row sums without a caller workspace.  The paper has no counterpart: this

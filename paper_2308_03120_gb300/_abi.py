@@ -104,3 +104,21 @@ SIGNATURES["coot_sum_rows_f32_static"] = (c_int, [_matp, _matp, c_void_p])
 SIGNATURES["coot_set_launch_config"] = (c_int, [c_int, c_int, c_int, c_int, c_int, c_int64])
 SIGNATURES["coot_last_launch"] = (c_int, [POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int64),
                                           POINTER(c_int64)])
+
+# learned launch shapes
+MODEL_FEATURES, MODEL_HIDDEN = 21, 64
+POLICY_BUILTIN, POLICY_LEARNED = 0, 1
+_fp = c_void_p  # float* (device or host buffer address)
+SIGNATURES.update({
+    "coot_mlp_forward": (c_int, [_fp, c_int, c_int, _fp, c_int, _fp, _fp, c_void_p]),
+    "coot_mlp_loss_grad": (c_int, [_fp, c_int, c_int, _fp, _fp, c_int, _fp, _fp, _fp, _fp, _fp, c_void_p]),
+    "coot_mlp_adam": (c_int, [_fp, _fp, _fp, _fp, c_int, c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, c_void_p]),
+    "coot_call_features": (c_int, [_u8p, c_size_t, c_int, POINTER(c_int32), c_int, c_uint, c_int64, c_int64, c_int,
+                                   c_int, c_int, c_int, c_int64, POINTER(ctypes.c_float)]),
+    "coot_model_load": (c_int, [POINTER(ctypes.c_float), c_size_t]),
+    "coot_model_predict": (c_int, [POINTER(ctypes.c_float), c_int, POINTER(ctypes.c_float)]),
+    "coot_set_policy": (c_int, [c_int]),
+    "coot_launch_candidates": (c_int, [c_int, POINTER(c_int32), c_int, POINTER(c_int)]),
+    "coot_prepare": (c_int, [_u8p, c_size_t, c_int, POINTER(c_int32), c_int, c_uint, c_int, c_int, c_int]),
+})

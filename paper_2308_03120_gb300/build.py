@@ -26,8 +26,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcoot.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-HOST_SOURCES = ["coot_api.cpp", "coot_tree.cpp", "coot_jit.cpp"]
-CUDA_SOURCES = ["coot_aot.cu", "coot_static.cu"]
+HOST_SOURCES = ["coot_api.cpp", "coot_tree.cpp", "coot_jit.cpp", "coot_policy.cpp"]
+CUDA_SOURCES = ["coot_aot.cu", "coot_static.cu", "coot_mlp.cu"]
 
 
 def cuda_home() -> str:

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "coot_internal.h"
 
@@ -171,9 +173,71 @@ static thread_local Launch g_override[5] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1,
 static thread_local Launch g_last;
 static thread_local int64_t g_last_grid = 0;
 
-static Launch heuristic(int kind, int n_in, const View& v) {
+static CallInfo call_info(int kind, const Tree& t, const coot_mat* in, int n_in, int out_dtype, unsigned heads,
+                          const View& v) {
+  CallInfo c;
+  c.kind = kind;
+  c.tree = &t;
+  c.in_bytes = 1;
+  for (int i = 0; i < n_in; ++i) c.in_bytes = std::max(c.in_bytes, dtype_size(in[i].dtype));
+  c.out_bytes = out_dtype >= 0 ? dtype_size(out_dtype) : 0;
+  c.heads = heads;
+  c.n_rows = in[0].n_rows;
+  c.n_cols = in[0].n_cols;
+  c.dense = true;
+  for (int i = 0; i < n_in; ++i) c.dense = c.dense && (in[i].ld == in[i].n_rows || in[i].n_cols <= 1);
+  (void)v;
+  return c;
+}
+
+// The learned policy's choice for a call: the candidate shape with the
+// lowest predicted time, cached per distinct call.
+static std::mutex g_choice_mu;
+static std::unordered_map<uint64_t, Launch> g_choice;
+
+static bool learned_choice(int kind, const View& v, const CallInfo& ci, Launch* out) {
+  if (kind > KIND_ROWSUM || policy() != COOT_POLICY_LEARNED || !model_ready()) return false;
+  const int64_t key_fields[] = {kind, ci.in_bytes, ci.out_bytes, (int64_t)ci.heads, ci.n_rows, ci.n_cols,
+                                ci.dense, pick_vec(v), device().id};
+  const uint64_t key = fnv1a(key_fields, sizeof key_fields, ci.tree->hash);
+  {
+    std::lock_guard<std::mutex> lock(g_choice_mu);
+    auto it = g_choice.find(key);
+    if (it != g_choice.end()) {
+      *out = it->second;
+      return true;
+    }
+  }
+  const int (*cand)[4] = nullptr;
+  const int n = candidates(kind, &cand);
+  double best = 0.0;
+  int best_i = -1;
+  float f[COOT_MODEL_FEATURES];
+  for (int i = 0; i < n; ++i) {
+    const int vec = cand[i][1] ? pick_vec(v, cand[i][1]) : pick_vec(v);
+    call_features(ci, cand[i][0], vec, cand[i][2], cand[i][3], f);
+    const double y = model_predict(f);
+    if (best_i < 0 || y < best) {
+      best = y;
+      best_i = i;
+    }
+  }
+  if (best_i < 0) return false;
+  Launch l;
+  l.block = cand[best_i][0];
+  l.vec = cand[best_i][1] ? pick_vec(v, cand[best_i][1]) : pick_vec(v);
+  l.unroll = cand[best_i][2];
+  l.split = cand[best_i][3];
+  std::lock_guard<std::mutex> lock(g_choice_mu);
+  g_choice[key] = l;
+  *out = l;
+  return true;
+}
+
+static Launch heuristic(int kind, int n_in, const View& v, const CallInfo* ci = nullptr) {
   Launch l;
   const Launch& o = g_override[kind];
+  if (!o.block && ci && learned_choice(kind, v, *ci, &l)) return l;
   // built-in choices, from exhaustive sweeps on GB300 (see the tuning
   // module): many bytes in flight per thread beat occupancy for these
   // streaming kernels
@@ -263,7 +327,8 @@ static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, u
   }
   const View v = make_view(in, n_in, store ? out : nullptr);
   const int kind = heads ? (store ? KIND_MAP : KIND_REDUCE) : KIND_MAP;
-  const Launch l = heuristic(kind, n_in, v);
+  const CallInfo ci = call_info(kind, t, in, n_in, store ? out->dtype : -1, heads, v);
+  const Launch l = heuristic(kind, n_in, v, &ci);
   KernelSpec spec;
   spec.kind = kind;
   for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
@@ -324,7 +389,8 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   }
   v.n = n_in;
   const int kind = dim == 0 ? KIND_COLSUM : KIND_ROWSUM;
-  Launch l = heuristic(kind, n_in, v);
+  const CallInfo ci = call_info(kind, t, in, n_in, -1, 0, v);
+  Launch l = heuristic(kind, n_in, v, &ci);
   const Device& d = device();
   KernelSpec spec;
   spec.kind = kind;
@@ -452,6 +518,58 @@ coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int
   o.blocks_per_sm = blocks_per_sm;
   o.split = split;
   g_override[kind] = o;
+  return COOT_OK;
+}
+
+coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_t* dtypes, int out_dtype,
+                         unsigned heads, int block, int vec, int unroll) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  if (kind < 0 || kind > 4 || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
+  if (block < 64 || block > 1024 || block % 64) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
+  if (!(vec == 1 || vec == 2 || vec == 4 || vec == 8) || unroll < 1 || unroll > 16)
+    return fail(COOT_ERR_INVALID_ARG, "vec must be 1, 2, 4 or 8 and unroll 1..16");
+  KernelSpec spec;
+  spec.kind = kind;
+  for (int i = 0; i < t.n_inputs; ++i) {
+    if (dtype_size(dtypes[i]) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
+    spec.in_dtype[i] = dtypes[i];
+  }
+  spec.out_dtype = out_dtype >= 0 ? out_dtype : 0;
+  spec.store = kind == KIND_MAP || kind == KIND_BATCHED;
+  spec.heads = (kind == KIND_MAP || kind == KIND_REDUCE) ? heads : 0;
+  spec.vec = vec;
+  spec.unroll = unroll;
+  spec.block = block;
+  spec.nc = true;
+  const Compiled* c = nullptr;
+  return kernel_for(t, spec, &c);
+}
+
+coot_status coot_call_features(const uint8_t* tree, size_t len, int kind, const int32_t* dtypes, int out_dtype,
+                               unsigned heads, int64_t n_rows, int64_t n_cols, int dense, int block, int vec,
+                               int unroll, int64_t split, float* features) {
+  clear_error();
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
+  if (s != COOT_OK) return s;
+  if (kind < 0 || kind > 3 || !dtypes || !features || block < 1) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
+  CallInfo c;
+  c.kind = kind;
+  c.tree = &t;
+  c.in_bytes = 1;
+  for (int i = 0; i < t.n_inputs; ++i) {
+    if (dtype_size(dtypes[i]) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
+    c.in_bytes = std::max(c.in_bytes, dtype_size(dtypes[i]));
+  }
+  c.out_bytes = out_dtype >= 0 ? dtype_size(out_dtype) : 0;
+  c.heads = heads;
+  c.n_rows = n_rows;
+  c.n_cols = n_cols;
+  c.dense = dense != 0;
+  call_features(c, block, vec, unroll, split, features);
   return COOT_OK;
 }
 

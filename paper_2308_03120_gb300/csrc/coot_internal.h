@@ -88,6 +88,26 @@ bool initialised();
 
 uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull);
 
+// ------------------------------------------------------------ learned launch shapes (coot_policy.cpp)
+
+// What the cost model sees of a call.
+struct CallInfo {
+  int kind = KIND_MAP;
+  const Tree* tree = nullptr;
+  int in_bytes = 4;   // widest input storage type
+  int out_bytes = 0;  // stored element-wise output, 0 if none
+  unsigned heads = 0;
+  int64_t n_rows = 0, n_cols = 0;
+  bool dense = true;
+};
+
+// Candidate shapes {block, vec, unroll, split} of a kind; returns the count.
+int candidates(int kind, const int (**out)[4]);
+void call_features(const CallInfo& c, int block, int vec, int unroll, int64_t split, float* f);
+bool model_ready();
+int policy();
+double model_predict(const float* features);
+
 }  // namespace coot
 
 // Launch-parameter block; identical layout to `coot_params` in jit_rt.cuh

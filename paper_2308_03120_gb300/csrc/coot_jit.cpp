@@ -13,6 +13,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <atomic>
 #include <cinttypes>
 #include <cstdio>
 #include <cstdlib>
@@ -84,7 +85,8 @@ static bool read_cache(const std::string& path, uint64_t key, std::string* cubin
 }
 
 static void write_cache(const std::string& path, uint64_t key, const std::string& cubin) {
-  const std::string tmp = path + ".tmp" + std::to_string(getpid());
+  static std::atomic<unsigned> serial{0};
+  const std::string tmp = path + ".tmp" + std::to_string(getpid()) + "." + std::to_string(serial++);
   FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return;
   CacheHeader h;
@@ -138,16 +140,21 @@ coot_status compile_only(const std::string& source, const std::string& arch, siz
 }
 
 coot_status get_kernel(const std::string& source, const KernelSpec& spec, const Compiled** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_init) return fail(COOT_ERR_NOT_INIT, "coot_init has not been called");
-  const std::string arch = arch_name(g_dev.cc_major, g_dev.cc_minor);
-  uint64_t key = fnv1a(source.data(), source.size());
-  key = fnv1a(arch.data(), arch.size(), key);
-  auto it = g_kernels.find(key);
-  if (it != g_kernels.end()) {
-    *out = &it->second;
-    return COOT_OK;
+  std::string arch;
+  uint64_t key;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_init) return fail(COOT_ERR_NOT_INIT, "coot_init has not been called");
+    arch = arch_name(g_dev.cc_major, g_dev.cc_minor);
+    key = fnv1a(source.data(), source.size());
+    key = fnv1a(arch.data(), arch.size(), key);
+    auto it = g_kernels.find(key);
+    if (it != g_kernels.end()) {
+      *out = &it->second;
+      return COOT_OK;
+    }
   }
+  // compile without holding the lock, so that threads compile in parallel
   std::string cubin;
   const std::string dir = cache_dir();
   char name[64];
@@ -160,6 +167,12 @@ coot_status get_kernel(const std::string& source, const KernelSpec& spec, const 
       mkdirs(dir);
       write_cache(path, key, cubin);
     }
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto again = g_kernels.find(key);
+  if (again != g_kernels.end()) {  // another thread finished first
+    *out = &again->second;
+    return COOT_OK;
   }
   cudaLibrary_t lib;
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
