@@ -351,7 +351,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t tree_len, const i
  *
  * Parameters: one FP32 array, W1 (d x h, row-major: W1[i * h + j] maps
  * input i to hidden unit j), b1 (h), W2 (h x h), b2 (h), w3 (h), b3 (1);
- * n = d h + h + h h + 3 h + 1.  Forward: h1 = relu(x W1 + b1), h2 =
+ * n = d h + h h + 3 h + 1.  Forward: h1 = relu(x W1 + b1), h2 =
  * relu(h1 W2 + b2), y = h2 . w3 + b3.
  * ---------------------------------------------------------------------- */
 

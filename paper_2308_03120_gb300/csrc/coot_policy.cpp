@@ -136,7 +136,8 @@ extern "C" {
 
 coot_status coot_model_load(const float* params, size_t n) {
   clear_error();
-  const size_t want = (size_t)COOT_MODEL_FEATURES * COOT_MODEL_HIDDEN + COOT_MODEL_HIDDEN +
+  // W1, b1, W2, b2, w3, b3
+  const size_t want = (size_t)COOT_MODEL_FEATURES * COOT_MODEL_HIDDEN +
                       (size_t)COOT_MODEL_HIDDEN * COOT_MODEL_HIDDEN + 3 * COOT_MODEL_HIDDEN + 1;
   if (params == nullptr || n != want)
     return fail(COOT_ERR_INVALID_ARG, "model needs " + std::to_string(want) + " parameters");

@@ -38,7 +38,7 @@ REDUCE_HEADS = 1 | 4      # sum and norm2
 
 
 def n_params(d: int = D, h: int = H) -> int:
-    return d * h + h + h * h + 3 * h + 1
+    return d * h + h * h + 3 * h + 1     # W1, W2, and b1, b2, w3, b3
 
 
 def candidates(kind: int):
