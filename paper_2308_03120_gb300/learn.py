@@ -21,6 +21,7 @@ import ctypes
 import json
 import math
 import os
+import pickle
 import time
 from concurrent.futures import ThreadPoolExecutor
 
@@ -214,17 +215,26 @@ class _Call:
                         self.n_cols, True, block, vec, unroll, split)
 
 
-def _time(fn, reps: int) -> float:
+def _time(fn, budget_us: float = 400.0) -> float:
+    """Mean device time of fn in microseconds: one warm call, a two-call
+    estimate, then enough calls for about budget_us of work (3..40)."""
     import torch
     fn()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
+    fn()
+    fn()
+    e1.record()
+    e1.synchronize()
+    est = e0.elapsed_time(e1) * 1e3 / 2
+    reps = int(min(40, max(3, budget_us / max(est, 1.0))))
+    e0.record()
     for _ in range(reps):
         fn()
     e1.record()
     e1.synchronize()
-    return e0.elapsed_time(e1) * 1e3 / reps  # microseconds
+    return e0.elapsed_time(e1) * 1e3 / reps
 
 
 def _shape(rng, max_log2: int):
@@ -237,7 +247,7 @@ def _shape(rng, max_log2: int):
     return r, c
 
 
-def generate(n_trees: int, seed: int, reps: int = 3, max_log2: int = 26, kinds_per_tree: int = 2,
+def generate(n_trees: int, seed: int, max_log2: int = 26, kinds_per_tree: int = 2,
              shapes_per_kind: int = 4, threads: int = 16, log=print):
     """Timing samples for n_trees random trees; every sample holds the
     per-candidate times (microseconds), features and the built-in time."""
@@ -281,18 +291,23 @@ def generate(n_trees: int, seed: int, reps: int = 3, max_log2: int = 26, kinds_p
     samples = []
     for i, (t, sexpr, n_in, k, dtype, (r, c)) in enumerate(plans):
         call = _Call(sexpr, n_in, k, dtype, r, c, seed * 7919 + i)
+        cands = candidates(k)
         rec = {"tree": t, "kind": k, "dtype": dtype, "n_rows": r, "n_cols": c, "n_inputs": n_in,
-               "cand": [], "us": [], "X": []}
-        for cfg in candidates(k):
-            block, vec, unroll, split = cfg
-            coot.coot_set_launch_config(k, block, vec, unroll, 0, split)
-            us = _time(call, reps)
-            last = coot.coot_last_launch()
-            rec["cand"].append(cfg)
-            rec["us"].append(us)
-            rec["X"].append(call.features(last["block"], last["vec"], last["unroll"], split))
-        coot.coot_set_launch_config(k, 0)
-        rec["builtin_us"] = _time(call, reps)
+               "cand": cands, "us_a": [0.0] * len(cands), "us_b": [0.0] * len(cands), "X": [None] * len(cands)}
+        # two independent passes (the second in reverse order): the tuner
+        # picks on pass a, every choice is scored on pass b
+        for pass_name, order in (("a", range(len(cands))), ("b", reversed(range(len(cands))))):
+            for j in order:
+                block, vec, unroll, split = cands[j]
+                coot.coot_set_launch_config(k, block, vec, unroll, 0, split)
+                rec["us_" + pass_name][j] = _time(call)
+                if rec["X"][j] is None:
+                    last = coot.coot_last_launch()
+                    rec["X"][j] = call.features(last["block"], last["vec"], last["unroll"], split)
+            coot.coot_set_launch_config(k, 0)
+            rec["builtin_" + pass_name] = _time(call)
+        rec["us"] = [(a + b) / 2 for a, b in zip(rec["us_a"], rec["us_b"])]
+        rec["builtin_us"] = (rec["builtin_a"] + rec["builtin_b"]) / 2
         samples.append(rec)
         del call
         if (i + 1) % 200 == 0:
@@ -309,21 +324,27 @@ def split_by_tree(samples, held_out_frac: float = 0.2, seed: int = 0):
 
 
 def design(samples):
+    """Rows (features, target): the target is log(t / t_builtin) of the same
+    call, so the model learns how each shape compares within a call (what
+    choosing needs) rather than absolute times spanning decades."""
     X = np.concatenate([np.stack(s["X"]) for s in samples]).astype(np.float32)
-    y = np.concatenate([np.log(np.maximum(np.asarray(s["us"]), 1e-3)) for s in samples]).astype(np.float32)
+    y = np.concatenate([np.log(np.maximum(np.asarray(s["us"]), 1e-3) / max(s["builtin_us"], 1e-3))
+                        for s in samples]).astype(np.float32)
     return X, y
 
 
 def regret(samples, predict) -> dict:
-    """Geometric-mean regret of the model's choice and of the built-in
-    shape against the fastest shape measured (candidates and built-in)."""
+    """Regret against the exhaustive tuner: the tuner takes the fastest
+    candidate of pass a; the model's choice, the built-in shape and the
+    tuner's choice are all scored on pass b (independent timings, so the
+    tuner's pick is not flattered by its own noise).  Geometric means."""
     rm, rb = [], []
     for s in samples:
-        us = np.asarray(s["us"])
-        best = min(us.min(), s["builtin_us"])
+        a, b = np.asarray(s["us_a"]), np.asarray(s["us_b"])
+        tuner = b[int(np.argmin(a))]
         pred = predict(np.stack(s["X"]))
-        rm.append(us[int(np.argmin(pred))] / best)
-        rb.append(s["builtin_us"] / best)
+        rm.append(b[int(np.argmin(pred))] / tuner)
+        rb.append(s["builtin_b"] / tuner)
     rm, rb = np.asarray(rm), np.asarray(rb)
     return {"samples": len(samples), "model_geomean": float(np.exp(np.mean(np.log(rm)))),
             "builtin_geomean": float(np.exp(np.mean(np.log(rb)))), "model_within_5pct": float(np.mean(rm <= 1.05)),
@@ -339,6 +360,8 @@ def main(argv=None):
     ap.add_argument("--max-log2", type=int, default=26)
     ap.add_argument("--out", default=None, help="report JSON path")
     ap.add_argument("--model", default=MODEL_PATH)
+    ap.add_argument("--data", default=None, help="save the timing samples here (pickle)")
+    ap.add_argument("--from-data", default=None, help="train on saved samples instead of measuring")
     args = ap.parse_args(argv)
     import torch
 
@@ -347,7 +370,14 @@ def main(argv=None):
     build.build()
     coot.coot_init(0)
     t0 = time.time()
-    samples = generate(args.trees, args.seed, max_log2=args.max_log2)
+    if args.from_data:
+        with open(args.from_data, "rb") as f:
+            samples = pickle.load(f)
+    else:
+        samples = generate(args.trees, args.seed, max_log2=args.max_log2)
+    if args.data:
+        with open(args.data, "wb") as f:
+            pickle.dump(samples, f)
     train, held = split_by_tree(samples)
     X, y = design(train)
     model = CostModel(seed=1)
