@@ -60,6 +60,43 @@ def peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "coot_tree.cpp", "coot_api.cpp")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "matrices_8192_traffic.md")
+
+
+def kernel_source_hash():
+    """sha256 over the sources that decide the matrix workload's kernels
+    (generated code, runtime, launch shapes)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2308_03120_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def committed_traffic(call):
+    """DRAM bytes (read + write) of one launch of `call` at 8192 x 8192 from
+    the committed ncu summary, or (None, why) when there is none or the
+    kernel sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            text = f.read()
+    except OSError:
+        return None, "no committed ncu traffic summary"
+    digest = None
+    for line in text.splitlines():
+        if line.startswith("kernel-source: sha256 "):
+            digest = line.split()[-1]
+    if digest != kernel_source_hash():
+        return None, "kernel sources changed since the ncu traffic capture"
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0] == call:
+            return int(cells[4]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 8192 x 8192"
+    return None, f"no traffic row for {call}"
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -373,6 +410,7 @@ def run_coot(args):
 
     peak, peak_kind = peaks()
     dom = max(names, key=lambda n: statistics.mean(per_call[n]))
+    traffic, traffic_note = committed_traffic(dom) if N == 8192 else (None, "traffic is captured at 8192 x 8192")
     dom_ms = statistics.mean(per_call[dom])
     achieved = STREAMS[dom] * MAT_BYTES / (dom_ms * 1e-3) / 1e9
     calls = {n: {"ms": round(statistics.mean(per_call[n]), 4),
@@ -401,7 +439,8 @@ def run_coot(args):
             "calls": calls,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None},
+                         "traffic": traffic, "traffic_note": traffic_note,
+                         "algorithmic_bytes": STREAMS[dom] * MAT_BYTES},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
@@ -596,6 +635,27 @@ def run_batched(args):
         "speedup_vs_per_matrix_graph": round(ms_per_graph / ms_graph, 1)}))
 
 
+def run_learned(args):
+    """Learned launch shapes on random trees the model never saw (fresh
+    seed): regret against the exhaustive tuner, model and built-in."""
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build, learn
+    _build.build()
+    coot.coot_init(0)
+    t0 = time.time()
+    samples = learn.generate(args.learned_trees, seed=4242, max_log2=26, log=lambda *a: None)
+    learn.load_policy()   # loads the model for host_predict
+    learn.use_builtin()
+    r = learn.regret(samples, learn.host_predict)
+    print(json.dumps({"metric": "learned launch-shape regret vs exhaustive tuner (geomean, lower is better)",
+                      "value": round(r["model_geomean"], 4), "unit": "ratio", "higher_is_better": False,
+                      "builtin": round(r["builtin_geomean"], 4), "target": 1.05,
+                      "model_within_5pct": round(r["model_within_5pct"], 3),
+                      "builtin_within_5pct": round(r["builtin_within_5pct"], 3),
+                      "samples": r["samples"], "unseen_trees": args.learned_trees,
+                      "seconds": round(time.time() - t0, 1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -603,16 +663,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="coot", choices=["coot", "reference"])
     ap.add_argument("--ref-cols", type=int, default=256, help="columns in each reference-arm step's sample")
-    ap.add_argument("--cpu-cols", type=int, default=1024, help="columns in the cpu_baseline sample")
+    ap.add_argument("--cpu-cols", type=int, default=4096, help="columns in the cpu_baseline sample")
+    ap.add_argument("--kernel-source-hash", action="store_true",
+                    help="print the digest of the kernel sources that committed traffic figures are tied to")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=8192, help="matrix order (8192 is the workload; smaller for profiling)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
+    ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
     ap.add_argument("--workload", default="matrices",
-                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched"],
+                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned"],
                     help="matrices is the headline line; the others print their own line")
     args = ap.parse_args()
+    if args.kernel_source_hash:
+        print(kernel_source_hash())
+        return
     global N, MAT_BYTES, STEP_BYTES
     N = args.n
     MAT_BYTES = N * N * ELEM
@@ -625,6 +691,8 @@ def main():
         run_precision(args, args.workload.split("-")[1])
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_coot(args)
 
