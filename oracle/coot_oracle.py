@@ -12,9 +12,13 @@ What it follows (Bandicoot, arXiv 2308.03120):
     element-wise division);
   * element-wise functions exp, log, sqrt, square: Table 7 ("misc(A)"); abs
     and negation are the unary forms of the same family;
+  * relational operators inside expressions ("A < x" and the other
+    relational expressions of Table 5's all/any rows);
   * reductions: Table 5 (accu = sum of all elements, dot of two objects with
-    equal element counts, norm(A, p)) and Table 6 (sum/min/max along dim 0 =
-    per column, dim 1 = per row);
+    equal element counts, norm(A, p), all(A) / any(A) = whether all / any
+    elements are nonzero) and Table 6 (sum/min/max along dim 0 = per
+    column, dim 1 = per row, and the statistics mean/stddev/var along a
+    dim);
   * column-major element order ("(i)" walks the matrix column by column,
     Table 1);
   * delayed evaluation (Section 7): the destination receives the value of
@@ -30,7 +34,17 @@ design notes of the repository):
   * norm with p = 2 of a matrix (more than one row and more than one column)
     is the spectral norm, which needs an SVD and is rejected; p = "fro" is
     the Frobenius norm; on a vector p = 2 is the Euclidean norm;
-  * empty inputs: accu, dot, norm and sums are 0; min/max raise EmptyError.
+  * empty inputs: accu, dot, norm and sums are 0; min/max raise EmptyError;
+    all() of nothing is true and any() of nothing is false;
+  * a relational node is 1 where the relation holds and 0 elsewhere, in the
+    compute type; NaN is unordered (every relation false except "!=");
+  * all/any test each element value, rounded to the compute type, against
+    zero (NaN is nonzero);
+  * var(A, norm_type, dim) divides by N - 1 (norm_type 0, the default) or by
+    N (norm_type 1), N the number of elements reduced; with N = 1 and
+    norm_type 0 it is 0; stddev is its square root; mean, var and stddev of
+    N = 0 elements are NaN; per-dim min/max round each element to the
+    compute type first, like the full min/max.
 
 Sums use math.fsum (the correctly rounded sum of the FP64 element values),
 so the only error in an oracle reduction is the rounding of each element's
@@ -57,6 +71,8 @@ import numpy as np
 #   ops:  0 input slot a | 1 constant imm | 2 neg a | 3 abs a | 4 exp a
 #         5 log a | 6 sqrt a | 7 square a | 8 a + b | 9 a - b
 #         10 a % b (element-wise product) | 11 a / b
+#         12 a < b | 13 a <= b | 14 a > b | 15 a >= b | 16 a == b | 17 a != b
+#            (1 where the relation holds, else 0)
 #   Operands name earlier nodes (a, b < i); the last node is the root.
 # --------------------------------------------------------------------------
 
@@ -66,10 +82,12 @@ MAX_NODES = 64
 MAX_INPUTS = 4
 
 OP_NAMES = {0: "x", 1: "c", 2: "neg", 3: "abs", 4: "exp", 5: "log", 6: "sqrt",
-            7: "square", 8: "add", 9: "sub", 10: "mul", 11: "div"}
+            7: "square", 8: "add", 9: "sub", 10: "mul", 11: "div",
+            12: "lt", 13: "le", 14: "gt", 15: "ge", 16: "eq", 17: "ne"}
 NAME_OPS = {v: k for k, v in OP_NAMES.items()}
 UNARY = {"neg", "abs", "exp", "log", "sqrt", "square"}
-BINARY = {"add", "sub", "mul", "div"}
+RELATIONAL = {"lt", "le", "gt", "ge", "eq", "ne"}
+BINARY = {"add", "sub", "mul", "div"} | RELATIONAL
 COMPUTE = {0: "f32", 3: "f64"}
 
 
@@ -315,8 +333,17 @@ def evaluate(tree, mats) -> np.ndarray:
                 v = vals[a] * vals[b]
             elif name == "div":
                 v = vals[a] / vals[b]
+            elif name in RELATIONAL:
+                v = np.where(_relate(name, vals[a], vals[b]), 1.0, 0.0)
             vals.append(v)
     return vals[-1]
+
+
+def _relate(name, x, y):
+    """The relation of a relational node (numpy comparisons are IEEE:
+    unordered operands make every relation false except !=)."""
+    return {"lt": np.less, "le": np.less_equal, "gt": np.greater, "ge": np.greater_equal,
+            "eq": np.equal, "ne": np.not_equal}[name](x, y)
 
 
 def evaluate_exact(sexpr, env: dict):
@@ -344,6 +371,9 @@ def evaluate_exact(sexpr, env: dict):
         return a * b
     if name == "div":
         return a / b
+    if name in RELATIONAL:
+        return Fraction(int({"lt": a < b, "le": a <= b, "gt": a > b, "ge": a >= b, "eq": a == b,
+                             "ne": a != b}[name]))
     raise ValueError(f"no exact form for {name}")
 
 
@@ -440,6 +470,16 @@ def error_bound(tree, mats):
                 e = np.where(ok, ex / (np.sqrt(np.abs(x)) + np.sqrt(np.maximum(x - ex, 0.0)) + 1e-300), 0.0)
                 e = np.where(ok & (ex == 0), 0.0, e) + np.where(ok, rnd(v, ulp["sqrt"]), 0.0)
                 unsafe |= ~(ok | certain_nan)
+            elif name in RELATIONAL:
+                # the result is exactly 0 or 1; it is certain where the
+                # operands' error intervals do not reach each other (or both
+                # operands are exact)
+                x, y, ex, ey = vals[a], vals[b], errs[a], errs[b]
+                v = np.where(_relate(name, x, y), 1.0, 0.0)
+                e = np.zeros(shape)
+                exact = (ex == 0) & (ey == 0)
+                apart = np.abs(x - y) > ex + ey
+                unsafe |= ~(exact | apart | np.isnan(x) | np.isnan(y))
             # values beyond the compute type's range overflow there but not here
             fin = np.isfinite(v)
             unsafe |= fin & (np.abs(v) > big)
@@ -535,3 +575,69 @@ def minmax(tree, mats) -> tuple[float, float]:
     if tree.compute == "f32":
         v = round_to_format(v, "f32")
     return float(np.min(v)), float(np.max(v))
+
+
+def _compute_values(tree: Tree, mats) -> np.ndarray:
+    """Element values rounded to the compute type (what a comparison with
+    zero or an extremum sees)."""
+    v = evaluate(tree, mats)
+    return round_to_format(v, "f32") if tree.compute == "f32" else v
+
+
+def all_(tree, mats) -> bool:
+    """all(expr): whether every element is nonzero (Table 5); NaN is
+    nonzero; true for an empty object."""
+    tree = _tree(tree)
+    return bool(np.all(_compute_values(tree, mats) != 0.0))
+
+
+def any_(tree, mats) -> bool:
+    """any(expr): whether some element is nonzero (Table 5); false for an
+    empty object."""
+    tree = _tree(tree)
+    return bool(np.any(_compute_values(tree, mats) != 0.0))
+
+
+STATS = ("sum", "mean", "var", "stddev", "min", "max")
+
+
+def stats_dim(tree, mats, dim: int, stat: str, norm_type: int = 0) -> np.ndarray:
+    """A statistic of each column (dim = 0, a 1 x n_cols result) or of each
+    row (dim = 1, an n_rows x 1 result) of expr (Table 6): sum, mean, var,
+    stddev, min or max.  var = sum((v - mean)^2) / (N - 1 + norm_type) with
+    the mean taken first (two passes), N the elements of the line."""
+    tree = _tree(tree)
+    if stat not in STATS:
+        raise ValueError(f"unknown statistic {stat!r}")
+    if dim not in (0, 1):
+        raise ValueError("dim must be 0 or 1")
+    if norm_type not in (0, 1):
+        raise ValueError("norm_type must be 0 or 1")
+    v = evaluate(tree, mats)
+    lines = [v[:, j] for j in range(v.shape[1])] if dim == 0 else [v[i, :] for i in range(v.shape[0])]
+    n = v.shape[0] if dim == 0 else v.shape[1]
+    if stat in ("min", "max"):
+        if n == 0 and lines:
+            raise EmptyError("min/max along a dim of length 0")
+        if tree.compute == "f32":
+            lines = [round_to_format(x, "f32") for x in lines]
+        f = np.min if stat == "min" else np.max
+        return np.array([float(f(x)) for x in lines])
+    out = []
+    for x in lines:
+        if stat == "sum":
+            out.append(_fsum(x))
+            continue
+        if n == 0:
+            out.append(math.nan)
+            continue
+        mean = _fsum(x) / n
+        if stat == "mean":
+            out.append(mean)
+            continue
+        if n == 1 and norm_type == 0:
+            var = 0.0 if np.isfinite(x).all() else math.nan
+        else:
+            var = _fsum((x - mean) ** 2) / (n - 1 + norm_type)
+        out.append(var if stat == "var" else math.sqrt(var) if var >= 0 else math.nan)
+    return np.array(out, dtype=np.float64)

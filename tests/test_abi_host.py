@@ -58,7 +58,7 @@ def _node(op, a=0, b=0, imm=0.0, z0=0, z1=0):
 MALFORMED = [
     _hdr(1, magic=b"COOX") + _node(0), _hdr(1, version=2) + _node(0), _hdr(0), _hdr(65) + _node(0) * 65,
     _hdr(1, n_inputs=0) + _node(0), _hdr(1, n_inputs=5) + _node(0), _hdr(1, compute=1) + _node(0),
-    _hdr(1, r0=1) + _node(0), _hdr(2) + _node(0), _hdr(1) + _node(12), _hdr(1) + _node(0, a=1),
+    _hdr(1, r0=1) + _node(0), _hdr(2) + _node(0), _hdr(1) + _node(200), _hdr(1) + _node(0, a=1),
     _hdr(2) + _node(0) + _node(2, a=1), _hdr(2) + _node(0) + _node(8, a=0, b=2),
     _hdr(2) + _node(0) + _node(2, a=0, b=1), _hdr(1) + _node(1, a=1, imm=1.0), _hdr(1) + _node(0, z0=1),
     b"COOT",

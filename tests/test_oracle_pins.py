@@ -72,7 +72,7 @@ def _node(op, a=0, b=0, imm=0.0, z0=0, z1=0):
     _hdr(1, compute=1) + _node(0),
     _hdr(1, r0=1) + _node(0),
     _hdr(2) + _node(0),                       # length mismatch
-    _hdr(1) + _node(12),                      # unknown op
+    _hdr(1) + _node(200),                     # unknown op
     _hdr(1) + _node(0, a=1),                  # slot >= n_inputs
     _hdr(2) + _node(0) + _node(2, a=1),       # self reference
     _hdr(2) + _node(0) + _node(8, a=0, b=2),  # forward reference
