@@ -60,13 +60,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "coot_tree.cpp", "coot_api.cpp")
+KERNEL_SOURCES = ("jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "matrices_8192_traffic.md")
 
 
 def kernel_source_hash():
-    """sha256 over the sources that decide the matrix workload's kernels
-    (generated code, runtime, launch shapes)."""
+    """sha256 over the device code of the matrix workload's kernels (the
+    runtime and the element-wise, column-sum and row-sum kernels)."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
@@ -75,10 +75,14 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def committed_traffic(call):
+def shape_text(last):
+    return "block {block} vec {vec} unroll {unroll} grid {grid} split {split}".format(**last)
+
+
+def committed_traffic(call, shape):
     """DRAM bytes (read + write) of one launch of `call` at 8192 x 8192 from
-    the committed ncu summary, or (None, why) when there is none or the
-    kernel sources changed since it was taken."""
+    the committed ncu summary, or (None, why) when there is none, or the
+    device code or the launch shape changed since it was taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             text = f.read()
@@ -92,7 +96,9 @@ def committed_traffic(call):
         return None, "kernel sources changed since the ncu traffic capture"
     for line in text.splitlines():
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 5 and cells[0] == call:
+        if len(cells) >= 8 and cells[0] == call:
+            if cells[7] != shape:
+                return None, f"launch shape changed since the ncu traffic capture ({cells[7]} -> {shape})"
             return int(cells[4]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 8192 x 8192"
     return None, f"no traffic row for {call}"
 
@@ -316,6 +322,15 @@ def run_coot(args):
     for _ in range(max(args.warmup, 3)):
         step()
     barrier()
+    # launch shape of each call (untimed)
+    shapes = {}
+    for i, n in enumerate(names):
+        [lambda: coot.coot_expr_reduce(t_expr, mats, heads, out=O1, out_dev=res, ws=ws),
+         lambda: coot.coot_expr_eval(t_chain, mats, O2, ws=ws),
+         lambda: coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws),
+         lambda: coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)][i]()
+        shapes[n] = shape_text(coot.coot_last_launch())
+    barrier()
     props = torch.cuda.get_device_properties(local)
     pci = None
     if hasattr(props, "pci_bus_id"):
@@ -410,11 +425,13 @@ def run_coot(args):
 
     peak, peak_kind = peaks()
     dom = max(names, key=lambda n: statistics.mean(per_call[n]))
-    traffic, traffic_note = committed_traffic(dom) if N == 8192 else (None, "traffic is captured at 8192 x 8192")
+    traffic, traffic_note = (committed_traffic(dom, shapes[dom]) if N == 8192
+                             else (None, "traffic is captured at 8192 x 8192"))
     dom_ms = statistics.mean(per_call[dom])
     achieved = STREAMS[dom] * MAT_BYTES / (dom_ms * 1e-3) / 1e9
     calls = {n: {"ms": round(statistics.mean(per_call[n]), 4),
-                 "gbs": round(STREAMS[n] * MAT_BYTES / (statistics.mean(per_call[n]) * 1e-3) / 1e9, 1)}
+                 "gbs": round(STREAMS[n] * MAT_BYTES / (statistics.mean(per_call[n]) * 1e-3) / 1e9, 1),
+                 "launch": shapes[n]}
              for n in names}
 
     cpu = None
@@ -439,7 +456,7 @@ def run_coot(args):
             "calls": calls,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": traffic, "traffic_note": traffic_note,
+                         "traffic": traffic, "traffic_note": traffic_note, "launch": shapes[dom],
                          "algorithmic_bytes": STREAMS[dom] * MAT_BYTES},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -635,6 +652,49 @@ def run_batched(args):
         "speedup_vs_per_matrix_graph": round(ms_per_graph / ms_graph, 1)}))
 
 
+def run_stats(args):
+    """All six statistics (sum, mean, var, stddev, min, max) of every column
+    and of every row of an 8192 x 8192 FP32 matrix in one pass per
+    dimension: of the stored matrix A (one input) and of the tree
+    (A%B+2C)/(1+|D|) (four inputs).  Algorithmic bytes: the inputs read once
+    plus 6 x 8192 FP32 results per call."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    seed = synth.BASE_SEED + 1
+    dev = [torch.from_numpy(h).cuda() for h in inputs_host(seed)]
+    mats = [coot.Mat(t, N, N, N) for t in dev]
+    ws = coot.Workspace(N)
+    outs = {d: [torch.empty(N, device="cuda") for _ in range(6)] for d in (0, 1)}
+    omats = {0: [coot.Mat(t, 1, N, 1) for t in outs[0]], 1: [coot.Mat(t, N, 1, N) for t in outs[1]]}
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    calls = {}
+    for name, sexpr, ins in (("leaf", synth.LEAF0, mats[:1]), ("tree", synth.MAT_EXPR, mats)):
+        tree = coot.serialize(sexpr)
+        for dim in (0, 1):
+            def fn(tree=tree, ins=ins, dim=dim):
+                coot.coot_stats_dim(tree, ins, dim, 0x3F, omats[dim], ws=ws)
+            ms = _timed(torch, stream, fn, args.steps, args.warmup)
+            nbytes = len(ins) * MAT_BYTES + 6 * N * 4
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            calls[f"{name}_dim{dim}"] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                         "launch": shape_text(coot.coot_last_launch())}
+    total_ms = sum(c["ms"] for c in calls.values())
+    total_bytes = sum((1 if k.startswith("leaf") else 4) * MAT_BYTES + 6 * N * 4 for k in calls)
+    dom = max(calls, key=lambda k: calls[k]["ms"])
+    print(json.dumps({"metric": "fused per-dim statistics HBM GB/s", "workload": f"matrices {N}x{N} fp32: "
+                      "sum/mean/var/stddev/min/max of every column and row, of A and of (A%B+2C)/(1+|D|)",
+                      "value": round(total_bytes / (total_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                      "frac_of_hbm_peak": round(total_bytes / (total_ms * 1e-3) / 1e9 / peak, 4),
+                      "peak": peak, "peak_kind": peak_kind, "calls": calls,
+                      "roofline": {"bound": "hbm", "kernel": dom, "achieved": calls[dom]["gbs"], "peak": peak,
+                                   "unit": "GB/s", "frac": calls[dom]["frac"]},
+                      "l2": "inputs larger than L2, no flush"}), flush=True)
+
+
 def run_learned(args):
     """Learned launch shapes on random trees the model never saw (fresh
     seed): regret against the exhaustive tuner, model and built-in."""
@@ -673,7 +733,7 @@ def main():
     ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
     ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
     ap.add_argument("--workload", default="matrices",
-                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned"],
+                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats"],
                     help="matrices is the headline line; the others print their own line")
     args = ap.parse_args()
     if args.kernel_source_hash:
@@ -693,6 +753,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "stats":
+        run_stats(args)
     else:
         run_coot(args)
 

@@ -138,7 +138,17 @@ typedef enum coot_op {
   COOT_OP_ADD = 8,    /* a + b       Table 2                               */
   COOT_OP_SUB = 9,    /* a - b       Table 2                               */
   COOT_OP_MUL = 10,   /* a % b       Table 2, element-wise (Schur) product */
-  COOT_OP_DIV = 11    /* a / b       Table 2, element-wise division        */
+  COOT_OP_DIV = 11,   /* a / b       Table 2, element-wise division        */
+  /* Relational operators (the "A < x" of Table 5's all/any rows, "other
+   * relational expressions may also be used"): 1 where the relation holds,
+   * else 0, in the compute type.  NaN is unordered: every relation with a
+   * NaN operand is false except COOT_OP_NE. */
+  COOT_OP_LT = 12,    /* a < b                                             */
+  COOT_OP_LE = 13,    /* a <= b                                            */
+  COOT_OP_GT = 14,    /* a > b                                             */
+  COOT_OP_GE = 15,    /* a >= b                                            */
+  COOT_OP_EQ = 16,    /* a == b                                            */
+  COOT_OP_NE = 17     /* a != b                                            */
 } coot_op;
 
 #define COOT_TREE_MAX_NODES 64
@@ -154,7 +164,12 @@ typedef enum coot_op {
 #define COOT_HEAD_MAX    (1u << 5) /* largest element (NaN propagates)         */
 #define COOT_HEAD_MINABS (1u << 6) /* smallest magnitude (norm p = "-inf")     */
 #define COOT_HEAD_MAXABS (1u << 7) /* largest magnitude (norm p = "inf")       */
-#define COOT_HEAD_ALL    0xFFu
+#define COOT_HEAD_ALL    (1u << 8) /* 1 if every element is nonzero, else 0
+                                      (all, Table 5; NaN is nonzero; 1 when
+                                      there are no elements)                 */
+#define COOT_HEAD_ANY    (1u << 9) /* 1 if some element is nonzero, else 0
+                                      (any, Table 5; 0 when there are none)  */
+#define COOT_HEAD_MASK   0x3FFu    /* every head bit                          */
 
 /* norm(A, p) selectors (Table 5): p = 1, 2, or one of these. */
 #define COOT_NORM_INF (-1)
@@ -189,7 +204,9 @@ int coot_version(void);
 coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
 
 /* Launch shape of the kernels of one kind (0 element-wise / with heads,
- * 1 reductions only, 2 column sums, 3 row sums, 4 batched) for the calls
+ * 1 reductions only, 2 column sums, 3 row sums, 4 batched, 5 column
+ * statistics, 6 row statistics; row statistics use at most 256 threads per
+ * block) for the calls
  * that follow ON THIS THREAD, for tuning and for the learned selection of
  * launch shapes (not in the paper).  block: threads per block, 64..1024 in
  * steps of 64, or 0 to drop the setting (back to the built-in choice);
@@ -198,7 +215,8 @@ coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
  * accesses in flight per thread and input, 1..16 (0 = built-in); for the
  * batched kind, rows in flight per lane; blocks_per_sm: cap on resident
  * blocks per SM for the persistent grid (0 = occupancy limit); split:
- * column sums: segments per column, row sums: column chunks (0 =
+ * column sums and statistics: segments per column, row sums and
+ * statistics: column chunks (0 =
  * chosen from the shape; capped by the workspace).  Host-only. */
 coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm,
                                    int64_t split);
@@ -235,7 +253,8 @@ coot_status coot_tree_compile(const uint8_t* tree, size_t tree_len, int kind, in
 /* Write the CUDA source generated for a tree into buf (NUL-terminated,
  * truncated to buf_len) and its full length to *len.  kind: 0 = element-wise
  * evaluation, 1 = full reduction, 2 = column sums, 3 = row sums,
- * 4 = batched evaluation; every input and the output FP32.  Host-only;
+ * 4 = batched evaluation, 5 / 6 = column / row statistics (all six); every
+ * input and the output FP32.  Host-only;
  * for inspection and tests. */
 coot_status coot_tree_source(const uint8_t* tree, size_t tree_len, int kind, char* buf,
                              size_t buf_len, size_t* len);
@@ -279,6 +298,13 @@ coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void
 coot_status coot_norm(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in, int p,
                       double* out_dev, void* ws, size_t ws_bytes, void* stream);
 
+/* out_dev[0] = all(tree(in...)), out_dev[1] = any(tree(in...)) (Table 5):
+ * 1.0 if every / some element value (in the compute type) is nonzero, else
+ * 0.0.  NaN counts as nonzero.  With a relational root this is all(A < x)
+ * and any(A < x).  Empty -> all 1.0, any 0.0. */
+coot_status coot_all_any(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                         double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
 /* out_dev[0] = min, out_dev[1] = max over all elements of tree(in...)
  * (Table 6, both dimensions).  Element values are in the compute type; a
  * NaN anywhere makes both results NaN.  Empty -> COOT_ERR_EMPTY. */
@@ -293,6 +319,35 @@ coot_status coot_minmax(const uint8_t* tree, size_t tree_len, const coot_mat* in
 coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
                              unsigned heads, const coot_mat* out, double* out_dev, void* ws,
                              size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Statistics along a dimension (Table 6: max/min/sum(A, dim) and the
+ * statistics mean/stddev/var(A, dim)), several in ONE pass over the inputs.
+ * ---------------------------------------------------------------------- */
+
+#define COOT_STAT_SUM    (1u << 0) /* sum of the line                        */
+#define COOT_STAT_MEAN   (1u << 1) /* sum / N                                */
+#define COOT_STAT_VAR    (1u << 2) /* sum((v - mean)^2) / (N - 1 + norm_type) */
+#define COOT_STAT_STDDEV (1u << 3) /* sqrt(var)                              */
+#define COOT_STAT_MIN    (1u << 4) /* smallest element (NaN propagates)      */
+#define COOT_STAT_MAX    (1u << 5) /* largest element (NaN propagates)       */
+#define COOT_STAT_MASK   0x3Fu
+
+/* Statistics of each line of tree(in...): dim = 0 -> of each column (every
+ * out[k] is 1 x n_cols), dim = 1 -> of each row (every out[k] is
+ * n_rows x 1).  `stats` is a nonzero mask of COOT_STAT_* bits; `out` is a
+ * host array of popcount(stats) device matrices, one per set bit in
+ * increasing bit order, all FP32 or all FP64, none overlapping an input or
+ * each other.  N is the line length (n_rows for dim 0, n_cols for dim 1).
+ * norm_type 0 divides the variance by N - 1 (var of one element is 0),
+ * norm_type 1 by N.  N = 0: sums are 0, mean / var / stddev NaN, and
+ * min / max COOT_ERR_EMPTY.  Element values and their sums follow the
+ * tree's compute type (sums exact per thread, combined as double-word
+ * numbers, finished in FP64); a line whose sum of squares leaves the compute
+ * type's range gets a NaN variance.  Results do not depend on timing. */
+coot_status coot_stats_dim(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
+                           int dim, unsigned stats, int norm_type, const coot_mat* out, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batched evaluation: many small matrices of uneven shapes in ONE launch.

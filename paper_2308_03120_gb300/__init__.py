@@ -21,15 +21,18 @@ from dataclasses import dataclass
 
 from . import _abi
 from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
-                   HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM, HEAD_SUMABS, HEAD_SUMSQ,
-                   KIND_BATCHED, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSUM, CootError, coot_mat)
-from .expr import Expr, abs_, const, exp, log, serialize, sqrt, square, var
+                   HEAD_ALL, HEAD_ANY, HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM,
+                   HEAD_SUMABS, HEAD_SUMSQ, KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE,
+                   KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
+                   CootError, coot_mat)
+from .expr import Expr, abs_, const, eq, exp, log, ne, serialize, sqrt, square, var
 
 __all__ = [
     "Mat", "Workspace", "CootError", "coot_init", "coot_finalize", "coot_workspace_size", "coot_tree_check",
     "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
-    "coot_norm", "coot_minmax", "coot_expr_reduce", "coot_unfused_eval", "coot_unfused_tmp_count",
-    "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "serialize",
+    "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_unfused_eval",
+    "coot_unfused_tmp_count", "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "eq", "ne",
+    "serialize",
     "batch_item", "coot_batch_plan", "coot_expr_eval_batched",
 ]
 
@@ -234,6 +237,28 @@ def coot_minmax(tree: bytes, ins, out_dev=None, ws=None, stream=None):
     _abi.call("coot_minmax", tree, len(tree), arr, n, ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
               _stream(stream))
     return res
+
+
+def coot_all_any(tree: bytes, ins, out_dev=None, ws=None, stream=None):
+    """[all, any] of the tree's elements as 1.0 / 0.0 (FP64 device tensor)."""
+    arr, n = _mats(ins)
+    w = _ws(ws, 0)
+    res = _result(out_dev, 2)
+    _abi.call("coot_all_any", tree, len(tree), arr, n, ctypes.c_void_p(res.data_ptr()), w.ptr, w.bytes,
+              _stream(stream))
+    return res
+
+
+def coot_stats_dim(tree: bytes, ins, dim: int, stats: int, outs, norm_type: int = 0, ws=None, stream=None) -> None:
+    """Statistics (STAT_* mask) of each column (dim 0) or row (dim 1) in one
+    pass; `outs` holds one Mat per set bit, in increasing bit order."""
+    arr, n = _mats(ins)
+    w = _ws(ws, ins[0].n_rows if dim == 1 else 0)
+    o_arr, n_out = _mats(outs)
+    if n_out != bin(stats & 0x3F).count("1"):
+        raise ValueError("one output per statistic")
+    _abi.call("coot_stats_dim", tree, len(tree), arr, n, dim, stats, norm_type, o_arr, w.ptr, w.bytes,
+              _stream(stream))
 
 
 def coot_unfused_eval(tree: bytes, ins, out: Mat, tmp=None, stream=None) -> None:

@@ -40,7 +40,7 @@ def cuda_home() -> str:
     raise RuntimeError("CUDA toolkit not found (set CUDA_HOME)")
 
 
-JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh"]
+JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh", "jit_stats.cuh"]
 
 
 def _embed_runtime() -> str:

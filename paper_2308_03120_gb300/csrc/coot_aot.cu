@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -154,7 +155,34 @@ __global__ void __launch_bounds__(256) node_kernel(int op, int nb, Operand a, Op
 
 int dsize(int dt) { return dt == COOT_F64 ? 8 : (dt == COOT_F32 ? 4 : 2); }
 
+// 1.0 in device memory: the source of device-to-device copies that write a
+// constant result (all() of an empty object) in stream order, also under
+// graph capture.
+__device__ const double g_one = 1.0;
+
 }  // namespace
+
+namespace coot {
+
+// Device address of a 1.0 (looked up once per device).
+coot_status device_one(const double** out) {
+  static std::mutex mu;
+  static const double* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return fail(COOT_ERR_CUDA, "no current device");
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_one);
+    if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    addr[dev] = static_cast<const double*>(p);
+  }
+  *out = addr[dev];
+  return COOT_OK;
+}
+
+}  // namespace coot
 
 extern "C" {
 

@@ -168,7 +168,8 @@ struct Launch {
 
 // A launch shape set by the caller for the calls that follow on this
 // thread (tuning, learned selection); block == 0 means "not set".
-static thread_local Launch g_override[5] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
+static thread_local Launch g_override[KIND_COUNT] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0},
+                                                     {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
 // The shape of the last launch on this thread.
 static thread_local Launch g_last;
 static thread_local int64_t g_last_grid = 0;
@@ -246,7 +247,7 @@ static Launch heuristic(int kind, int n_in, const View& v, const CallInfo* ci = 
   if (kind == KIND_ROWSUM) {
     l.block = 512;
     l.unroll = n_in >= 3 ? 4 : 8;
-  } else if (kind == KIND_COLSUM) {
+  } else if (kind == KIND_COLSUM || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) {
     l.unroll = 4;
   } else {
     l.unroll = n_in >= 3 ? 4 : 8;
@@ -273,14 +274,14 @@ static void fill_io(coot_params_host* p, const View& v, int n_in) {
 }
 
 static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, const Launch& l, coot_params_host* p,
-                          void* stream) {
+                          void* stream, void* kernel_params = nullptr) {
   int bps = std::max(1, c->max_blocks_per_sm);
   if (l.blocks_per_sm > 0) bps = std::min(bps, l.blocks_per_sm);
   int64_t grid = (int64_t)device().sm_count * bps;
   grid = std::min(grid, std::max<int64_t>(units, 1));
   grid = std::min(grid, max_grid);
   grid = std::max<int64_t>(grid, 1);
-  void* args[] = {p};
+  void* args[] = {kernel_params ? kernel_params : (void*)p};
   cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(l.block), args, 0,
                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -307,8 +308,17 @@ static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, u
     if (res == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
     if (n == 0) {
       if (heads & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
+      // sums and norms of nothing are 0, any() is 0, all() is 1
       cudaError_t e = cudaMemsetAsync(res, 0, sizeof(double) * popcount(heads), (cudaStream_t)stream);
       if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+      if (heads & COOT_HEAD_ALL) {
+        const double* one = nullptr;
+        coot_status s = device_one(&one);
+        if (s != COOT_OK) return s;
+        e = cudaMemcpyAsync(res + popcount(heads & (COOT_HEAD_ALL - 1)), one, sizeof(double),
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+      }
       return COOT_OK;
     }
     if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * popcount(heads))
@@ -459,6 +469,119 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   return launch(c, units, INT32_MAX, l, &p, stream);
 }
 
+// Statistics of each column (dim 0) or row (dim 1): the column / row sum
+// kernels' work division, with a partial of NC components per line.
+static coot_status run_stats_dim(const Tree& t, const coot_mat* in, int n_in, int dim, unsigned stats, int norm_type,
+                                 const coot_mat* out, void* ws, size_t ws_bytes, void* stream) {
+  if (dim != 0 && dim != 1) return fail(COOT_ERR_INVALID_ARG, "dim must be 0 or 1");
+  if (stats == 0 || (stats & ~COOT_STAT_MASK)) return fail(COOT_ERR_INVALID_ARG, "stats must be a nonzero COOT_STAT_* mask");
+  if (norm_type != 0 && norm_type != 1) return fail(COOT_ERR_INVALID_ARG, "norm_type must be 0 or 1");
+  if (out == nullptr) return fail(COOT_ERR_INVALID_ARG, "outputs are NULL");
+  const int64_t R = in[0].n_rows, Cn = in[0].n_cols;
+  const int64_t lines = dim == 0 ? Cn : R, N = dim == 0 ? R : Cn;
+  int n_out = 0;
+  for (unsigned m = stats; m; m &= m - 1) ++n_out;
+  for (int k = 0; k < n_out; ++k) {
+    coot_status s = check_mat(&out[k], "output");
+    if (s != COOT_OK) return s;
+    if (dim == 0 ? (out[k].n_rows != 1 || out[k].n_cols != Cn) : (out[k].n_rows != R || out[k].n_cols != 1))
+      return fail(COOT_ERR_SHAPE, dim == 0 ? "statistics along dim 0 are 1 x n_cols" : "statistics along dim 1 are n_rows x 1");
+    if (out[k].dtype != COOT_F32 && out[k].dtype != COOT_F64)
+      return fail(COOT_ERR_DTYPE, "statistics are stored as FP32 or FP64");
+    if (out[k].dtype != out[0].dtype) return fail(COOT_ERR_DTYPE, "every statistics output needs the same dtype");
+    bool aliased = false;
+    s = check_alias(out[k], in, n_in, false, &aliased);
+    if (s != COOT_OK) return s;
+    s = check_alias(out[k], out, k, false, &aliased);
+    if (s != COOT_OK) return fail(COOT_ERR_ALIAS, "statistics outputs overlap each other");
+  }
+  if (lines == 0) return COOT_OK;
+  if (N == 0 && (stats & (COOT_STAT_MIN | COOT_STAT_MAX)))
+    return fail(COOT_ERR_EMPTY, "min/max along a dimension of length 0");
+  View v;
+  v.n_rows = R;
+  v.n_cols = Cn;
+  for (int i = 0; i < n_in; ++i) {
+    v.ptr[i] = in[i].ptr;
+    v.ld[i] = in[i].ld;
+    v.dtype[i] = in[i].dtype;
+  }
+  v.n = n_in;
+  const int kind = dim == 0 ? KIND_COLSTATS : KIND_ROWSTATS;
+  Launch l = heuristic(kind, n_in, v);
+  const int real = t.compute == COOT_F64 ? 8 : 4;
+  if (kind == KIND_ROWSTATS) {
+    // the block's shared partials: at most 256 threads and 16-byte rows
+    l.block = std::min(l.block, 256);
+    l.vec = std::min(l.vec, pick_vec(v, 16 / real));
+  }
+  const Device& d = device();
+  KernelSpec spec;
+  spec.kind = kind;
+  for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
+  spec.out_dtype = out[0].dtype;
+  spec.heads = stats;
+  spec.vec = l.vec;
+  spec.unroll = l.unroll;
+  spec.block = l.block;
+  spec.nc = true;
+  const Compiled* c = nullptr;
+  coot_status s = kernel_for(t, spec, &c);
+  if (s != COOT_OK) return s;
+  coot_stats_params_host sp;
+  std::memset(&sp, 0, sizeof sp);
+  fill_io(&sp.b, v, n_in);
+  sp.b.ws = (unsigned char*)ws;
+  int k = 0;
+  for (int b = 0; b < 6; ++b) {
+    if (!(stats & (1u << b))) continue;
+    sp.out[k] = out[k].ptr;
+    sp.inc[k] = dim == 0 ? out[k].ld : 1;
+    ++k;
+  }
+  sp.norm_type = norm_type;
+  // components of a partial: the sum, the shifted sum and the shifted sum
+  // of squares as pairs, min, max
+  const bool s1 = stats & (COOT_STAT_SUM | COOT_STAT_MEAN);
+  const bool dv = stats & (COOT_STAT_VAR | COOT_STAT_STDDEV);
+  const int64_t entry = (2 * s1 + 4 * dv + !!(stats & COOT_STAT_MIN) + !!(stats & COOT_STAT_MAX)) * real;
+  const int64_t resident = (int64_t)d.sm_count * std::max(1, c->max_blocks_per_sm);
+  const size_t part_bytes = ws ? (ws_bytes > COOT_WS_PARTIALS_OFF ? ws_bytes - COOT_WS_PARTIALS_OFF : 0) : 0;
+  int64_t units;
+  if (dim == 0) {
+    const int64_t warps = l.block / 32;
+    const int64_t wt = 32LL * l.vec * l.unroll;
+    const int64_t target = 3 * resident * warps / 2;
+    int64_t S = 1;
+    if (Cn < target && R > wt && Cn <= COOT_WS_MAX_COUNTERS) S = std::min<int64_t>((target + Cn - 1) / Cn, (R + wt - 1) / wt);
+    if (l.split > 0) S = std::min<int64_t>(l.split, std::max<int64_t>((R + wt - 1) / wt, 1));
+    if (Cn > COOT_WS_MAX_COUNTERS) S = 1;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(part_bytes / (entry * std::max<int64_t>(Cn, 1)))));
+    int64_t rps = (R + S - 1) / S;
+    rps = std::max<int64_t>(((rps + wt - 1) / wt) * wt, wt);
+    if (S > 1) S = std::max<int64_t>((R + rps - 1) / rps, 1);
+    sp.b.split = S;
+    sp.b.rows_per_split = rps;
+    units = (Cn * S + warps - 1) / warps;
+  } else {
+    const int64_t groups = std::max(1, l.block / 64);
+    const int64_t panel = 64LL * l.vec;
+    const int64_t n_panels = (R + panel - 1) / panel;
+    const int64_t target = 3 * (int64_t)d.sm_count / 2;
+    int64_t C = std::max<int64_t>(1, (target + n_panels - 1) / n_panels);
+    if (l.split > 0) C = l.split;
+    C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));
+    C = std::min<int64_t>(C, COOT_MAX_ROW_CHUNKS);
+    C = std::min<int64_t>(C, (int64_t)(part_bytes / (entry * std::max<int64_t>(R, 1))));
+    if (n_panels > COOT_WS_MAX_COUNTERS) C = 1;
+    C = std::max<int64_t>(C, 1);
+    sp.b.split = C;
+    units = n_panels * C;
+  }
+  if (sp.b.split > 1 && ws == nullptr) return fail(COOT_ERR_WORKSPACE, "split statistics need a workspace");
+  return launch(c, units, INT32_MAX, l, &sp.b, stream, &sp);
+}
+
 }  // namespace coot
 
 using namespace coot;
@@ -501,7 +624,7 @@ int coot_version(void) { return 100; }
 
 coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm, int64_t split) {
   clear_error();
-  if (kind < 0 || kind > 4) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..4");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..6");
   if (block == 0) {
     g_override[kind] = Launch{1, 1, 0};
     return COOT_OK;
@@ -527,7 +650,7 @@ coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_
   Tree t;
   coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
-  if (kind < 0 || kind > 4 || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
+  if (kind < 0 || kind >= KIND_COUNT || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
   if (block < 64 || block > 1024 || block % 64) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
   if (!(vec == 1 || vec == 2 || vec == 4 || vec == 8) || unroll < 1 || unroll > 16)
     return fail(COOT_ERR_INVALID_ARG, "vec must be 1, 2, 4 or 8 and unroll 1..16");
@@ -539,7 +662,7 @@ coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_
   }
   spec.out_dtype = out_dtype >= 0 ? out_dtype : 0;
   spec.store = kind == KIND_MAP || kind == KIND_BATCHED;
-  spec.heads = (kind == KIND_MAP || kind == KIND_REDUCE) ? heads : 0;
+  spec.heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
   spec.vec = vec;
   spec.unroll = unroll;
   spec.block = block;
@@ -605,13 +728,13 @@ coot_status coot_tree_check(const uint8_t* tree, size_t len, int* n_inputs, int*
 }
 
 static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype, unsigned heads, KernelSpec* spec) {
-  if (kind < 0 || kind > 3) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..3");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..6");
   if (dtype_size(in_dtype) == 0 || dtype_size(out_dtype) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
   spec->kind = kind;
   for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
   spec->out_dtype = out_dtype;
-  spec->store = kind == KIND_MAP;
-  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE) ? heads : 0;
+  spec->store = kind == KIND_MAP || kind == KIND_BATCHED;
+  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
   spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
   spec->unroll = 2;
   spec->block = 256;
@@ -624,7 +747,8 @@ coot_status coot_tree_source(const uint8_t* tree, size_t len, int kind, char* bu
   coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
   KernelSpec spec;
-  s = spec_for(t, kind, COOT_F32, COOT_F32, kind == KIND_REDUCE ? COOT_HEAD_SUM : 0, &spec);
+  const unsigned heads = kind == KIND_REDUCE ? COOT_HEAD_SUM : (kind >= KIND_COLSTATS ? COOT_STAT_MASK : 0);
+  s = spec_for(t, kind, COOT_F32, COOT_F32, heads, &spec);
   if (s != COOT_OK) return s;
   const std::string src = generate_source(t, spec);
   if (out_len) *out_len = src.size();
@@ -665,7 +789,7 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t len, const coot_mat* in
   Tree t;
   coot_status s = check_operands(tree, len, in, n_in, &t);
   if (s != COOT_OK) return s;
-  if (heads & ~COOT_HEAD_ALL) return fail(COOT_ERR_INVALID_ARG, "unknown head bits");
+  if (heads & ~COOT_HEAD_MASK) return fail(COOT_ERR_INVALID_ARG, "unknown head bits");
   if (heads == 0 && out == nullptr) return fail(COOT_ERR_INVALID_ARG, "nothing to compute");
   return run_map_reduce(t, in, n_in, heads, out, out_dev, ws, ws_bytes, stream);
 }
@@ -716,6 +840,24 @@ coot_status coot_sum_dim(const uint8_t* tree, size_t len, const coot_mat* in, in
   coot_status s = check_operands(tree, len, in, n_in, &t);
   if (s != COOT_OK) return s;
   return run_sum_dim(t, in, n_in, dim, out, ws, ws_bytes, stream);
+}
+
+coot_status coot_stats_dim(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int dim, unsigned stats,
+                           int norm_type, const coot_mat* out, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  return run_stats_dim(t, in, n_in, dim, stats, norm_type, out, ws, ws_bytes, stream);
+}
+
+coot_status coot_all_any(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
+                         size_t ws_bytes, void* stream) {
+  clear_error();
+  Tree t;
+  coot_status s = check_operands(tree, len, in, n_in, &t);
+  if (s != COOT_OK) return s;
+  return run_map_reduce(t, in, n_in, COOT_HEAD_ALL | COOT_HEAD_ANY, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------ batched evaluation

@@ -36,7 +36,16 @@ struct Tree {
 coot_status parse_tree(const uint8_t* buf, size_t len, Tree* out);
 
 // Kernel kinds (the prelude's COOT_KIND).
-enum Kind { KIND_MAP = 0, KIND_REDUCE = 1, KIND_COLSUM = 2, KIND_ROWSUM = 3, KIND_BATCHED = 4 };
+enum Kind {
+  KIND_MAP = 0,
+  KIND_REDUCE = 1,
+  KIND_COLSUM = 2,
+  KIND_ROWSUM = 3,
+  KIND_BATCHED = 4,
+  KIND_COLSTATS = 5,
+  KIND_ROWSTATS = 6,
+  KIND_COUNT = 7
+};
 
 // Everything that selects one compiled kernel.
 struct KernelSpec {
@@ -88,6 +97,9 @@ bool initialised();
 
 uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull);
 
+// Device address of a constant 1.0 on the current device (coot_aot.cu).
+coot_status device_one(const double** out);
+
 // ------------------------------------------------------------ learned launch shapes (coot_policy.cpp)
 
 // What the cost model sees of a call.
@@ -127,6 +139,16 @@ struct coot_params_host {
   int64_t n_work;
 };
 static_assert(sizeof(coot_params_host) == 8 * 18, "coot_params layout");
+
+// Launch parameters of the statistics kernels; identical layout to
+// `coot_stats_params` in jit_stats.cuh.
+struct coot_stats_params_host {
+  coot_params_host b;
+  void* out[6];
+  int64_t inc[6];
+  int64_t norm_type;
+};
+static_assert(sizeof(coot_stats_params_host) == 8 * 31, "coot_stats_params layout");
 
 // Workspace layout (offsets in bytes), mirrored in jit_rt.cuh.
 #define COOT_WS_COUNTER_OFF 128

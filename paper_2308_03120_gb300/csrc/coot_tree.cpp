@@ -40,7 +40,7 @@ static double rdf64(const uint8_t* p) {
 }
 
 static bool is_unary(int op) { return op >= COOT_OP_NEG && op <= COOT_OP_SQUARE; }
-static bool is_binary(int op) { return op >= COOT_OP_ADD && op <= COOT_OP_DIV; }
+static bool is_binary(int op) { return op >= COOT_OP_ADD && op <= COOT_OP_NE; }
 
 coot_status parse_tree(const uint8_t* buf, size_t len, Tree* out) {
   if (buf == nullptr) return fail(COOT_ERR_INVALID_ARG, "tree is NULL");
@@ -133,6 +133,13 @@ static std::string tree_function(const Tree& t) {
       case COOT_OP_SUB: e = a + " - " + b; break;
       case COOT_OP_MUL: e = a + " * " + b; break;
       case COOT_OP_DIV: e = a + " / " + b; break;
+      // relational nodes: 1 or 0 (IEEE comparisons: NaN is unordered)
+      case COOT_OP_LT: e = "(" + a + " < " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_LE: e = "(" + a + " <= " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_GT: e = "(" + a + " > " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_GE: e = "(" + a + " >= " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_EQ: e = "(" + a + " == " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_NE: e = "(" + a + " != " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
     }
     s += "  const COOT_REAL t" + std::to_string(k) + " = " + e + ";\n";
   }
@@ -146,6 +153,8 @@ const char* entry_name(const KernelSpec& spec) {
     case KIND_REDUCE: return "coot_reduce";
     case KIND_COLSUM: return "coot_colsum";
     case KIND_ROWSUM: return "coot_rowsum";
+    case KIND_COLSTATS: return "coot_colstats";
+    case KIND_ROWSTATS: return "coot_rowstats";
     default: return "coot_batched";
   }
 }

@@ -6,12 +6,14 @@
 // after a prelude that defines
 //   COOT_KIND     0 element-wise evaluation (optionally with reductions),
 //                 1 full reductions only, 2 column sums, 3 row sums,
-//                 4 batched evaluation over a work list
+//                 4 batched evaluation over a work list, 5 column
+//                 statistics, 6 row statistics
 //   COOT_NIN      number of input slots (1..4)
 //   COOT_TI0..3   storage code of each input (0 FP32, 1 BF16, 2 FP16, 3 FP64)
 //   COOT_TO       storage code of the stored output
 //   COOT_STORE    1 if element values are stored
-//   COOT_HEADS    mask of reduction heads (COOT_HEAD_* in coot.h)
+//   COOT_HEADS    mask of reduction heads (COOT_HEAD_* in coot.h); for the
+//                 statistics kinds the mask of statistics (COOT_STAT_*)
 //   COOT_REAL     float or double (the tree's compute type)
 //   COOT_VEC      elements per vector access, COOT_UNROLL vectors in flight
 //                 per thread and input, COOT_BLOCK threads per block
@@ -63,6 +65,8 @@ struct coot_params {
 #define COOT_HEAD_MAX (1u << 5)
 #define COOT_HEAD_MINABS (1u << 6)
 #define COOT_HEAD_MAXABS (1u << 7)
+#define COOT_HEAD_ALL (1u << 8)
+#define COOT_HEAD_ANY (1u << 9)
 
 #define COOT_WARPS (COOT_BLOCK / 32)
 #define COOT_INF_F __int_as_float(0x7f800000)
@@ -434,9 +438,17 @@ __device__ __forceinline__ COOT_REAL coot_pairwise(const COOT_REAL* y, int what)
 #ifndef COOT_HEADS
 #define COOT_HEADS 0
 #endif
+#if COOT_KIND == 0 || COOT_KIND == 1
 #define COOT_NHEADS (((COOT_HEADS >> 0) & 1) + ((COOT_HEADS >> 1) & 1) + ((COOT_HEADS >> 2) & 1) + \
                      ((COOT_HEADS >> 3) & 1) + ((COOT_HEADS >> 4) & 1) + ((COOT_HEADS >> 5) & 1) + \
-                     ((COOT_HEADS >> 6) & 1) + ((COOT_HEADS >> 7) & 1))
+                     ((COOT_HEADS >> 6) & 1) + ((COOT_HEADS >> 7) & 1) + ((COOT_HEADS >> 8) & 1) + \
+                     ((COOT_HEADS >> 9) & 1))
+#else
+#define COOT_NHEADS 0
+#endif
+
+// all / any: 1 for a nonzero value (NaN included), else 0
+__device__ __forceinline__ COOT_REAL coot_nonzero(COOT_REAL y) { return y != (COOT_REAL)0 ? (COOT_REAL)1 : (COOT_REAL)0; }
 
 struct coot_acc {
   COOT_REAL s, sc;   // sum
@@ -444,11 +456,12 @@ struct coot_acc {
   COOT_REAL a, ac;   // sum of magnitudes
   COOT_REAL mn, mx;  // min, max
   COOT_REAL mna, mxa;  // min, max magnitude
+  COOT_REAL alz, anz;  // all: smallest nonzero indicator; any: largest
 
   __device__ __forceinline__ void init() {
     s = sc = q = qc = a = ac = (COOT_REAL)0;
-    mn = mna = (COOT_REAL)COOT_INF_F;
-    mx = -(COOT_REAL)COOT_INF_F;
+    mn = mna = alz = (COOT_REAL)COOT_INF_F;
+    mx = anz = -(COOT_REAL)COOT_INF_F;
     mxa = (COOT_REAL)0;
   }
   __device__ __forceinline__ void add(COOT_REAL y) {
@@ -459,6 +472,8 @@ struct coot_acc {
     if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y);
     if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
     if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
+    if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y));
+    if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y));
   }
   // V consecutive values.  The plain sum adds every value with TwoSum (no
   // rounding is lost however the terms cancel).  Sums of squares and of
@@ -477,6 +492,8 @@ struct coot_acc {
       if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
       if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y[v]));
+      if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y[v]));
+      if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y[v]));
     }
   }
   // per-head values as FP64, in head-bit order
@@ -492,6 +509,8 @@ struct coot_acc {
     if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) { h[k] = mx; l[k] = 0; ++k; }
     if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) { h[k] = mna; l[k] = 0; ++k; }
     if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) { h[k] = mxa; l[k] = 0; ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) { h[k] = alz; l[k] = 0; ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) { h[k] = anz; l[k] = 0; ++k; }
     (void)k;
   }
 };
@@ -503,30 +522,38 @@ __device__ __forceinline__ unsigned coot_head_bit(int k) {
   return m & (~m + 1);
 }
 
+// heads combined by a minimum / a maximum (the rest are sums)
+__device__ __forceinline__ bool coot_min_head(unsigned bit) {
+  return bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS || bit == COOT_HEAD_ALL;
+}
+__device__ __forceinline__ bool coot_max_head(unsigned bit) {
+  return bit == COOT_HEAD_MAX || bit == COOT_HEAD_MAXABS || bit == COOT_HEAD_ANY;
+}
+
 __device__ __forceinline__ double coot_combine(unsigned bit, double a, double b) {
-  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return coot_min(a, b);
-  if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_MAXABS) return coot_max(a, b);
+  if (coot_min_head(bit)) return coot_min(a, b);
+  if (coot_max_head(bit)) return coot_max(a, b);
   return a + b;
 }
 
 __device__ __forceinline__ double coot_identity(unsigned bit) {
-  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return COOT_INF_D;
-  if (bit == COOT_HEAD_MAX) return -COOT_INF_D;
+  if (coot_min_head(bit)) return COOT_INF_D;
+  if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_ANY) return -COOT_INF_D;
   return 0.0;
 }
 
 #if COOT_NHEADS > 0
 __device__ __forceinline__ COOT_REAL coot_identity_r(unsigned bit) {
-  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) return (COOT_REAL)COOT_INF_F;
-  if (bit == COOT_HEAD_MAX) return -(COOT_REAL)COOT_INF_F;
+  if (coot_min_head(bit)) return (COOT_REAL)COOT_INF_F;
+  if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_ANY) return -(COOT_REAL)COOT_INF_F;
   return (COOT_REAL)0;
 }
 
 // head `bit`'s combine of two double-word values
 __device__ __forceinline__ void coot_combine_dw(unsigned bit, COOT_REAL& h, COOT_REAL& l, COOT_REAL yh, COOT_REAL yl) {
-  if (bit == COOT_HEAD_MIN || bit == COOT_HEAD_MINABS) {
+  if (coot_min_head(bit)) {
     h = coot_min(h, yh);
-  } else if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_MAXABS) {
+  } else if (coot_max_head(bit)) {
     h = coot_max(h, yh);
   } else {
     coot_dw_add(h, l, yh, yl);
@@ -599,7 +626,11 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
       w = lane < COOT_WARPS ? red64[lane] : coot_identity(bit);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) w = coot_combine(bit, w, __shfl_down_sync(0xffffffffu, w, o));
-      if (lane == 0) p.res[k] = (bit == COOT_HEAD_NORM2) ? sqrt(w) : w;
+      // norm2 is the root of its sum; all / any become 1 or 0 (an empty
+      // object leaves the identities +inf / -inf)
+      if (lane == 0)
+        p.res[k] = (bit == COOT_HEAD_NORM2) ? sqrt(w)
+                   : (bit == COOT_HEAD_ALL || bit == COOT_HEAD_ANY) ? (w > 0.0 ? 1.0 : 0.0) : w;
     }
   }
   if (threadIdx.x == 0) *(coot_u32*)(p.ws + COOT_WS_COUNTER_OFF) = 0u;

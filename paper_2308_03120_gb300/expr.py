@@ -11,6 +11,9 @@ evaluates in one fused kernel.  The operators mirror the paper's Table 2:
     x / y, x / k, k / x                   element-wise division
     -x
 and Table 7's element-wise functions exp, log, sqrt, square, plus abs.
+Relational expressions (Table 5's "A < x" inside all/any) build 1/0
+nodes: x < y, x <= y, x > y, x >= y, and eq(x, y), ne(x, y) (Python's ==
+and != keep their usual meaning on expression objects).
 `x * y` of two expressions is a matrix product in Armadillo and is refused
 here (matrix multiplication is not an element-wise operation).
 """
@@ -19,7 +22,9 @@ from __future__ import annotations
 import struct
 
 _OPS = {"x": 0, "c": 1, "neg": 2, "abs": 3, "exp": 4, "log": 5, "sqrt": 6, "square": 7,
-        "add": 8, "sub": 9, "mul": 10, "div": 11}
+        "add": 8, "sub": 9, "mul": 10, "div": 11,
+        "lt": 12, "le": 13, "gt": 14, "ge": 15, "eq": 16, "ne": 17}
+_BINARY = ("add", "sub", "mul", "div", "lt", "le", "gt", "ge", "eq", "ne")
 
 
 class Expr:
@@ -79,6 +84,18 @@ class Expr:
     def __abs__(self):
         return Expr("abs", (self,))
 
+    def __lt__(self, o):
+        return Expr("lt", (self, Expr._wrap(o)))
+
+    def __le__(self, o):
+        return Expr("le", (self, Expr._wrap(o)))
+
+    def __gt__(self, o):
+        return Expr("gt", (self, Expr._wrap(o)))
+
+    def __ge__(self, o):
+        return Expr("ge", (self, Expr._wrap(o)))
+
     # ---- nested-tuple form and serialisation
     def sexpr(self):
         if self.op == "x":
@@ -129,6 +146,16 @@ def abs_(e):
     return Expr("abs", (Expr._wrap(e),))
 
 
+def eq(a, b):
+    """1 where a == b, else 0."""
+    return Expr("eq", (Expr._wrap(a), Expr._wrap(b)))
+
+
+def ne(a, b):
+    """1 where a != b (NaN included), else 0."""
+    return Expr("ne", (Expr._wrap(a), Expr._wrap(b)))
+
+
 def as_expr(sexpr) -> Expr:
     """Expr from the nested-tuple form (("x", k), ("c", v), (op, a[, b]))."""
     op = sexpr[0]
@@ -155,7 +182,7 @@ def serialize(sexpr, compute: str = "f32", n_inputs: int | None = None) -> bytes
             rec = (_OPS["c"], 0, 0, float(t[1]))
         elif op in ("neg", "abs", "exp", "log", "sqrt", "square"):
             rec = (_OPS[op], walk(t[1]), 0, 0.0)
-        elif op in ("add", "sub", "mul", "div"):
+        elif op in _BINARY:
             a = walk(t[1])
             b = walk(t[2])
             rec = (_OPS[op], a, b, 0.0)

@@ -121,13 +121,22 @@ def test_generated_source_inlines_the_tree():
     assert "exp(" in src64 and "#define COOT_REAL double" in src64
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("dt", [0, 1, 2, 3])
 def test_every_kernel_kind_compiles_for_sm103a(kind, dt):
     t = serialize(synth.MAT_CHAIN, compute="f64" if dt == 3 else "f32")
-    heads = 0xFF if kind in (0, 1) else 0
-    n = coot.coot_tree_compile(t, kind=kind, in_dtype=dt, out_dtype=dt, heads=heads if kind == 1 else 0)
+    heads = {1: 0x3FF, 5: 0x3F, 6: 0x3F}.get(kind, 0)
+    out_dt = dt if kind < 5 else (3 if dt == 3 else 0)
+    n = coot.coot_tree_compile(t, kind=kind, in_dtype=dt, out_dtype=out_dt, heads=heads)
     assert n > 1000
+
+
+def test_relational_trees_compile():
+    x = coot.var(0)
+    t = ((x < 0.5) % x + coot.eq(x, 1.0) - (x >= -1.0)).tree()
+    src = coot.coot_tree_source(t, 0)
+    assert " < " in src and " == " in src and " >= " in src
+    assert coot.coot_tree_compile(t, kind=1, heads=0x300) > 1000
 
 
 def test_injected_compile_failure_is_a_status(monkeypatch):
@@ -191,7 +200,34 @@ def test_reduction_argument_errors():
     a, b = _fake(1, 6), _fake(5, 1, ptr=1 << 24)
     st, _ = _call("coot_dot", ctypes.byref(a), ctypes.byref(b), res, None, 0, None)
     assert _abi.STATUS[st] == "COOT_ERR_SHAPE"
+    st, msg = _call("coot_expr_reduce", leaf, len(leaf), m, 1, 1 << 10, None, res, None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "head" in msg
 
+
+def test_stats_argument_errors():
+    leaf = serialize(synth.LEAF0)
+    m = (_abi.coot_mat * 1)(_fake(30, 40))
+    ws = ctypes.c_void_p(1 << 32)
+
+    def stats(dim, mask, outs, norm_type=0, ins=m):
+        arr = (_abi.coot_mat * len(outs))(*outs)
+        st, msg = _call("coot_stats_dim", leaf, len(leaf), ins, 1, dim, mask, norm_type, arr, ws, 1 << 22, None)
+        return _abi.STATUS[st], msg
+
+    row = lambda k, dt=0: _fake(1, 40, ptr=(1 << 28) + k * 4096, dtype=dt)  # noqa: E731
+    assert stats(0, 0, [row(0)])[0] == "COOT_ERR_INVALID_ARG"                  # no statistic
+    assert stats(0, 1 << 6, [row(0)])[0] == "COOT_ERR_INVALID_ARG"             # unknown bit
+    assert stats(2, 1, [row(0)])[0] == "COOT_ERR_INVALID_ARG"                  # dim
+    assert stats(0, 1, [row(0)], norm_type=2)[0] == "COOT_ERR_INVALID_ARG"     # norm_type
+    assert stats(1, 1, [row(0)])[0] == "COOT_ERR_SHAPE"                        # dim 1 wants 30 x 1
+    assert stats(0, 1, [row(0, dt=1)])[0] == "COOT_ERR_DTYPE"                  # BF16 statistics
+    assert stats(0, 3, [row(0), row(1, dt=3)])[0] == "COOT_ERR_DTYPE"          # mixed dtypes
+    st, msg = stats(0, 3, [row(0), _fake(1, 40, ptr=(1 << 28) + 8)])
+    assert st == "COOT_ERR_ALIAS"                                               # outputs overlap
+    assert stats(0, 1, [_fake(1, 40, ptr=(1 << 20) + 64)])[0] == "COOT_ERR_ALIAS"  # overlaps the input
+    empty = (_abi.coot_mat * 1)(_fake(0, 5))
+    st, _ = stats(0, 16, [_fake(1, 5, ptr=1 << 28)], ins=empty)
+    assert st == "COOT_ERR_EMPTY"
 
 def test_device_calls_need_init():
     # valid arguments that reach the kernel cache: refused without coot_init
