@@ -10,8 +10,12 @@ What it follows (Bandicoot, arXiv 2308.03120):
   * element-wise operators and scalar operators: Table 2 ("A + k", "k - A",
     "A * k", "A + B", "A - B", "A % B" element-wise product, "A / B"
     element-wise division);
-  * element-wise functions exp, log, sqrt, square: Table 7 ("misc(A)"); abs
+  * element-wise functions exp, log, sqrt, square, pow, log10: Table 7
+    ("misc(A)"); cos, sin, tan, acos, asin, atan: Table 7 ("trig(A)"); abs
     and negation are the unary forms of the same family;
+  * storage types: FP32, BF16, FP16, FP64 and the integer types int32 and
+    uint32 (Section 7's conversion example reads an integer matrix into a
+    float expression);
   * relational operators inside expressions ("A < x" and the other
     relational expressions of Table 5's all/any rows);
   * reductions: Table 5 (accu = sum of all elements, dot of two objects with
@@ -29,6 +33,13 @@ Readings where the paper is silent (each is listed with its reason in the
 design notes of the repository):
   * immediates are stored as FP64 in the tree and rounded to the compute
     type before use (for FP32 compute: nearest FP32), on both sides;
+  * an input is converted to the compute type when it is read: FP64, int32
+    and uint32 values are rounded to the nearest FP32 for an FP32 tree
+    (exact up to 2^24 for the integers); every type is exact in FP64;
+  * an integer output receives the value rounded toward zero, saturated to
+    the type's range, with NaN stored as 0;
+  * pow(a, b) follows C's pow (IEEE 754 pown/powr special cases: pow(x, 0)
+    = 1 even for NaN x, a negative base with a non-integer exponent is NaN);
   * min/max propagate NaN; for FP32 compute each element value is rounded to
     FP32 before the extremum is taken (a comparison adds no rounding);
   * norm with p = 2 of a matrix (more than one row and more than one column)
@@ -73,6 +84,8 @@ import numpy as np
 #         10 a % b (element-wise product) | 11 a / b
 #         12 a < b | 13 a <= b | 14 a > b | 15 a >= b | 16 a == b | 17 a != b
 #            (1 where the relation holds, else 0)
+#         18 pow(a, b) | 19 log10 a | 20 sin a | 21 cos a | 22 tan a
+#         23 asin a | 24 acos a | 25 atan a
 #   Operands name earlier nodes (a, b < i); the last node is the root.
 # --------------------------------------------------------------------------
 
@@ -83,11 +96,14 @@ MAX_INPUTS = 4
 
 OP_NAMES = {0: "x", 1: "c", 2: "neg", 3: "abs", 4: "exp", 5: "log", 6: "sqrt",
             7: "square", 8: "add", 9: "sub", 10: "mul", 11: "div",
-            12: "lt", 13: "le", 14: "gt", 15: "ge", 16: "eq", 17: "ne"}
+            12: "lt", 13: "le", 14: "gt", 15: "ge", 16: "eq", 17: "ne",
+            18: "pow", 19: "log10", 20: "sin", 21: "cos", 22: "tan", 23: "asin", 24: "acos", 25: "atan"}
 NAME_OPS = {v: k for k, v in OP_NAMES.items()}
-UNARY = {"neg", "abs", "exp", "log", "sqrt", "square"}
+UNARY = {"neg", "abs", "exp", "log", "sqrt", "square", "log10", "sin", "cos", "tan", "asin", "acos", "atan"}
 RELATIONAL = {"lt", "le", "gt", "ge", "eq", "ne"}
-BINARY = {"add", "sub", "mul", "div"} | RELATIONAL
+BINARY = {"add", "sub", "mul", "div", "pow"} | RELATIONAL
+_NUMPY_UNARY = {"log10": np.log10, "sin": np.sin, "cos": np.cos, "tan": np.tan, "asin": np.arcsin,
+                "acos": np.arccos, "atan": np.arctan}
 COMPUTE = {0: "f32", 3: "f64"}
 
 
@@ -231,7 +247,25 @@ def decode_storage(buf: np.ndarray, dtype: str) -> np.ndarray:
     if dtype == "bf16":
         # a BF16 number is the upper half of the FP32 number with the same bits
         return (buf.view(np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+    if dtype == "i32":
+        return buf.view(np.int32).astype(np.float64)
+    if dtype == "u32":
+        return buf.view(np.uint32).astype(np.float64)
     raise ValueError(dtype)
+
+
+INT_RANGE = {"i32": (-2.0 ** 31, 2.0 ** 31 - 1), "u32": (0.0, 2.0 ** 32 - 1)}
+
+
+def to_integer(v64, dtype: str) -> np.ndarray:
+    """FP64 values -> the integer storage type: rounded toward zero,
+    saturated to the type's range, NaN -> 0 (the values as FP64)."""
+    lo, hi = INT_RANGE[dtype]
+    v = np.asarray(v64, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        t = np.trunc(v)
+        t = np.where(np.isnan(v), 0.0, np.clip(t, lo, hi))
+    return t
 
 
 def round_to_format(v, fmt: str) -> np.ndarray:
@@ -264,6 +298,8 @@ def encode_storage(v64: np.ndarray, dtype: str) -> np.ndarray:
     if dtype == "bf16":
         f = v64.astype(np.float32).view(np.uint32)
         return (f >> np.uint32(16)).astype(np.uint16)
+    if dtype in ("i32", "u32"):
+        return to_integer(v64, dtype).astype(np.int32 if dtype == "i32" else np.uint32)
     raise ValueError(dtype)
 
 
@@ -305,7 +341,7 @@ def evaluate(tree, mats) -> np.ndarray:
     """Value of the expression at every element, in FP64."""
     tree = _tree(tree)
     shape = _check_shapes(tree, mats)
-    xs = [logical(m) for m in mats]
+    xs = [leaf_values(tree, m) for m in mats]
     vals = []
     with np.errstate(all="ignore"):
         for name, a, b, imm in tree.nodes:
@@ -335,8 +371,22 @@ def evaluate(tree, mats) -> np.ndarray:
                 v = vals[a] / vals[b]
             elif name in RELATIONAL:
                 v = np.where(_relate(name, vals[a], vals[b]), 1.0, 0.0)
+            elif name == "pow":
+                v = np.power(vals[a], vals[b])
+            elif name in _NUMPY_UNARY:
+                v = _NUMPY_UNARY[name](vals[a])
             vals.append(v)
     return vals[-1]
+
+
+def leaf_values(tree: Tree, mat) -> np.ndarray:
+    """An input as the compute type reads it: storage types wider than FP32's
+    24-bit significand (FP64, int32, uint32) are rounded to the nearest FP32
+    for an FP32 tree; everything is exact in FP64."""
+    v = logical(mat)
+    if tree.compute == "f32" and mat.dtype in ("f64", "i32", "u32"):
+        v = round_to_format(v, "f32")
+    return v
 
 
 def _relate(name, x, y):
@@ -384,8 +434,12 @@ def evaluate_exact(sexpr, env: dict):
 # accuracy of the device functions, in units in the last place of the result,
 # as documented for CUDA's single and double precision maths (without fast
 # maths: IEEE-rounded add, multiply, divide and square root)
-ULPS = {"f32": {"exp": 2.0, "log": 1.0, "sqrt": 0.5, "op": 0.5},
-        "f64": {"exp": 1.0, "log": 1.0, "sqrt": 0.5, "op": 0.5}}
+# (taken at or above the documented figures: where a figure is not certain
+# the larger one is used, which only widens the tolerance)
+ULPS = {"f32": {"exp": 2.0, "log": 1.0, "sqrt": 0.5, "op": 0.5, "log10": 2.0, "sin": 2.0, "cos": 2.0,
+                "tan": 4.0, "asin": 4.0, "acos": 4.0, "atan": 2.0, "pow": 8.0},
+        "f64": {"exp": 1.0, "log": 1.0, "sqrt": 0.5, "op": 0.5, "log10": 2.0, "sin": 2.0, "cos": 2.0,
+                "tan": 2.0, "asin": 2.0, "acos": 2.0, "atan": 2.0, "pow": 2.0}}
 
 
 def error_bound(tree, mats):
@@ -406,7 +460,7 @@ def error_bound(tree, mats):
     eta = 2.0 ** (emin - p + 1)                     # subnormal spacing
     big = (2.0 - 2.0 ** (1 - p)) * 2.0 ** emax
     ulp = ULPS[fmt]
-    xs = [logical(m) for m in mats]
+    xs = [leaf_values(tree, m) for m in mats]
     vals, errs = [], []
     unsafe = np.zeros(shape, dtype=bool)
 
@@ -470,6 +524,64 @@ def error_bound(tree, mats):
                 e = np.where(ok, ex / (np.sqrt(np.abs(x)) + np.sqrt(np.maximum(x - ex, 0.0)) + 1e-300), 0.0)
                 e = np.where(ok & (ex == 0), 0.0, e) + np.where(ok, rnd(v, ulp["sqrt"]), 0.0)
                 unsafe |= ~(ok | certain_nan)
+            elif name == "log10":
+                x, ex = vals[a], errs[a]
+                v = np.log10(x)
+                ok = x - ex > 0
+                certain_nan = (x + ex < 0) | np.isnan(x)
+                certain_zero = (x == 0) & (ex == 0)
+                e = np.where(ok, -np.log1p(-np.minimum(ex / np.where(ok, x, 1.0), 0.5)) / math.log(10.0), 0.0)
+                e = np.where(ok & (ex > 0.5 * x), np.inf, e) + np.where(ok, rnd(v, ulp["log10"]), 0.0)
+                unsafe |= ~(ok | certain_nan | certain_zero)
+            elif name in ("sin", "cos"):
+                # both are 1-Lipschitz and bounded by 1
+                x, ex = vals[a], errs[a]
+                v = np.sin(x) if name == "sin" else np.cos(x)
+                e = np.minimum(ex, 2.0) + rnd(v, ulp[name])
+            elif name == "tan":
+                # the operand's interval must not reach a pole pi/2 + k pi;
+                # tan is monotonic between poles, so its slope 1 + tan^2 is
+                # largest at an end of the interval
+                x, ex = vals[a], errs[a]
+                v = np.tan(x)
+                k_lo = np.floor((x - ex) / np.pi - 0.5)
+                k_hi = np.floor((x + ex) / np.pi - 0.5)
+                ok = (k_lo == k_hi) | (ex == 0)
+                slope = 1.0 + np.maximum(np.tan(x - ex) ** 2, np.tan(x + ex) ** 2)
+                e = np.where(ok, ex * slope, 0.0) + rnd(v, ulp["tan"])
+                unsafe |= ~(ok | np.isnan(x))
+            elif name in ("asin", "acos"):
+                # slope 1 / sqrt(1 - x^2): the interval must stay inside
+                # (-1, 1) unless the operand is exact
+                x, ex = vals[a], errs[a]
+                v = np.arcsin(x) if name == "asin" else np.arccos(x)
+                ax = np.abs(x)
+                ok = ax + ex < 1.0
+                exact = (ex == 0) & (ax <= 1.0)
+                certain_nan = (ax - ex > 1.0) | np.isnan(x)
+                slope = 1.0 / np.sqrt(np.maximum(1.0 - (ax + ex) ** 2, 1e-300))
+                e = np.where(ok, ex * slope, 0.0) + np.where(ok | exact, rnd(v, ulp[name]), 0.0)
+                unsafe |= ~(ok | exact | certain_nan)
+            elif name == "atan":
+                x, ex = vals[a], errs[a]
+                v = np.arctan(x)
+                e = ex / (1.0 + np.maximum(np.abs(x) - ex, 0.0) ** 2) + rnd(v, ulp["atan"])
+            elif name == "pow":
+                # x^y = exp(y ln|x|) (sign from an integer y): relative
+                # perturbations multiply it by at most
+                # exp(|y| ex / (|x| - ex) + |ln|x|| ey)
+                x, y, ex, ey = vals[a], vals[b], errs[a], errs[b]
+                v = np.power(x, y)
+                ax = np.abs(x)
+                y_int = (ey == 0) & (np.floor(y) == y)
+                base_ok = (ax - ex > 0) & ((x > 0) | y_int)
+                exact = (ex == 0) & (ey == 0)
+                zero_base = (x == 0) & (ex == 0) & ((y - ey > 0) | (y + ey < 0))
+                rel = np.abs(y) * ex / np.where(base_ok, ax - ex, 1.0) + \
+                    np.abs(np.log(np.where(base_ok, ax, 1.0))) * ey
+                e = np.where(base_ok & ~exact, np.abs(v) * np.expm1(np.minimum(rel, 700.0)), 0.0)
+                e = e + rnd(v, ulp["pow"])
+                unsafe |= ~(base_ok | exact | zero_base | np.isnan(x) | np.isnan(y))
             elif name in RELATIONAL:
                 # the result is exactly 0 or 1; it is certain where the
                 # operands' error intervals do not reach each other (or both
