@@ -695,6 +695,47 @@ def run_stats(args):
                       "l2": "inputs larger than L2, no flush"}), flush=True)
 
 
+def run_convert(args):
+    """Fused type conversion (Section 7: an integer matrix converted and
+    used in one float expression): B = 2 A + 1 with A an 8192 x 8192 int32
+    matrix and B FP32, in one kernel (read 4 B, write 4 B per element),
+    against converting first into an FP32 temporary and then evaluating the
+    expression (read 4, write 4, read 4, write 4)."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    u = synth.uniform01(synth.BASE_SEED + 5, N * N)
+    a = torch.from_numpy(np.floor(-1e6 + u * 2e6).astype(np.int32)).cuda()
+    tmp = torch.empty(N * N, device="cuda")
+    out = torch.empty(N * N, device="cuda")
+    A, T, B = (coot.Mat(t, N, N, N) for t in (a, tmp, out))
+    expr = coot.serialize(("add", ("mul", synth.C(2.0), synth.X(0)), synth.C(1.0)))
+    leaf = coot.serialize(synth.LEAF0)
+    stream = torch.cuda.current_stream()
+
+    def fused():
+        coot.coot_expr_eval(expr, [A], B)
+
+    def two_step():
+        coot.coot_expr_eval(leaf, [A], T)
+        coot.coot_expr_eval(expr, [T], B)
+
+    ms_f = _timed(torch, stream, fused, args.steps, args.warmup)
+    ms_u = _timed(torch, stream, two_step, args.steps, args.warmup)
+    peak, peak_kind = peaks()
+    fused_bytes = 8 * N * N
+    print(json.dumps({"metric": "fused int32->fp32 conversion + expression", "workload":
+                      f"B = 2 A + 1, A {N}x{N} int32, B fp32", "unit": "ms",
+                      "fused_ms": round(ms_f, 4), "two_step_ms": round(ms_u, 4),
+                      "fusion_speedup": round(ms_u / ms_f, 3),
+                      "fused_gbs": round(fused_bytes / (ms_f * 1e-3) / 1e9, 1),
+                      "frac_of_hbm_peak": round(fused_bytes / (ms_f * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+                      "two_step_gbs": round(2 * fused_bytes / (ms_u * 1e-3) / 1e9, 1),
+                      "l2": "inputs larger than L2, no flush"}), flush=True)
+
+
 def run_learned(args):
     """Learned launch shapes on random trees the model never saw (fresh
     seed): regret against the exhaustive tuner, model and built-in."""
@@ -733,7 +774,7 @@ def main():
     ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
     ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
     ap.add_argument("--workload", default="matrices",
-                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats"],
+                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats", "convert"],
                     help="matrices is the headline line; the others print their own line")
     args = ap.parse_args()
     if args.kernel_source_hash:
@@ -755,6 +796,8 @@ def main():
         run_learned(args)
     elif args.workload == "stats":
         run_stats(args)
+    elif args.workload == "convert":
+        run_convert(args)
     else:
         run_coot(args)
 

@@ -85,7 +85,15 @@ typedef enum coot_dtype {
   COOT_F32 = 0,
   COOT_BF16 = 1,
   COOT_F16 = 2,
-  COOT_F64 = 3
+  COOT_F64 = 3,
+  /* Integer storage (Section 7's conversion example reads an integer matrix
+   * into a float expression): converted to the compute type on load (to
+   * the nearest FP32 for an FP32 tree, exact up to 2^24; exact in FP64).
+   * As element-wise outputs they receive the value rounded toward zero,
+   * saturated to the type's range, NaN stored as 0.  Sums, statistics and
+   * column sums are not stored in integer types. */
+  COOT_I32 = 4,
+  COOT_U32 = 5
 } coot_dtype;
 
 /* A column-major matrix in device memory: element (i, j), 0 <= i < n_rows,
@@ -148,7 +156,18 @@ typedef enum coot_op {
   COOT_OP_GT = 14,    /* a > b                                             */
   COOT_OP_GE = 15,    /* a >= b                                            */
   COOT_OP_EQ = 16,    /* a == b                                            */
-  COOT_OP_NE = 17     /* a != b                                            */
+  COOT_OP_NE = 17,    /* a != b                                            */
+  /* Table 7: pow and log10 ("misc(A)") and the trigonometric functions
+   * ("trig(A)"), in the compute type's CUDA functions (no fast maths; pow
+   * follows C's pow for the special cases). */
+  COOT_OP_POW = 18,   /* pow(a, b)                                         */
+  COOT_OP_LOG10 = 19, /* log10(a)                                          */
+  COOT_OP_SIN = 20,   /* sin(a)                                            */
+  COOT_OP_COS = 21,   /* cos(a)                                            */
+  COOT_OP_TAN = 22,   /* tan(a)                                            */
+  COOT_OP_ASIN = 23,  /* asin(a)                                           */
+  COOT_OP_ACOS = 24,  /* acos(a)                                           */
+  COOT_OP_ATAN = 25   /* atan(a)                                           */
 } coot_op;
 
 #define COOT_TREE_MAX_NODES 64

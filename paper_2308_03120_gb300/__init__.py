@@ -20,19 +20,21 @@ import ctypes
 from dataclasses import dataclass
 
 from . import _abi
-from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
+from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_I32, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
+                   COOT_U32,
                    HEAD_ALL, HEAD_ANY, HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM,
                    HEAD_SUMABS, HEAD_SUMSQ, KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE,
                    KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
                    CootError, coot_mat)
-from .expr import Expr, abs_, const, eq, exp, log, ne, serialize, sqrt, square, var
+from .expr import (Expr, abs_, acos, asin, atan, const, cos, eq, exp, log, log10, ne, pow_, serialize, sin, sqrt,
+                   square, tan, var)
 
 __all__ = [
     "Mat", "Workspace", "CootError", "coot_init", "coot_finalize", "coot_workspace_size", "coot_tree_check",
     "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
     "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_unfused_eval",
     "coot_unfused_tmp_count", "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "eq", "ne",
-    "serialize",
+    "pow_", "log10", "sin", "cos", "tan", "asin", "acos", "atan", "serialize",
     "batch_item", "coot_batch_plan", "coot_expr_eval_batched",
 ]
 
@@ -44,7 +46,9 @@ def _dtype_code(t) -> int:
     import torch
     if _TORCH_DTYPES is None:
         _TORCH_DTYPES = {torch.float32: COOT_F32, torch.bfloat16: COOT_BF16, torch.float16: COOT_F16,
-                         torch.float64: COOT_F64}
+                         torch.float64: COOT_F64, torch.int32: COOT_I32}
+        if hasattr(torch, "uint32"):
+            _TORCH_DTYPES[torch.uint32] = COOT_U32
     try:
         return _TORCH_DTYPES[t.dtype]
     except KeyError:

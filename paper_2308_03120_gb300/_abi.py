@@ -8,7 +8,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcoot.so")
 
-COOT_F32, COOT_BF16, COOT_F16, COOT_F64 = 0, 1, 2, 3
+COOT_F32, COOT_BF16, COOT_F16, COOT_F64, COOT_I32, COOT_U32 = 0, 1, 2, 3, 4, 5
 COOT_NORM_INF, COOT_NORM_NEG_INF, COOT_NORM_FRO = -1, -2, -3
 HEAD_SUM, HEAD_SUMSQ, HEAD_NORM2, HEAD_SUMABS = 1, 2, 4, 8
 HEAD_MIN, HEAD_MAX, HEAD_MINABS, HEAD_MAXABS = 16, 32, 64, 128

@@ -42,6 +42,8 @@ __device__ __forceinline__ R load_as(const Operand& o, int64_t i, int64_t j) {
       const unsigned short h = ((const unsigned short*)o.ptr)[idx];
       return (R)__uint_as_float(((unsigned)h) << 16);
     }
+    case COOT_I32: return (R)((const int*)o.ptr)[idx];
+    case COOT_U32: return (R)((const unsigned*)o.ptr)[idx];
     default: {
       const unsigned short h = ((const unsigned short*)o.ptr)[idx];
       float f;
@@ -49,6 +51,28 @@ __device__ __forceinline__ R load_as(const Operand& o, int64_t i, int64_t j) {
       return (R)f;
     }
   }
+}
+
+// integer storage: rounded toward zero, saturated, NaN -> 0
+__device__ __forceinline__ int to_s32(float v) {
+  int r;
+  asm("cvt.rzi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ int to_s32(double v) {
+  int r;
+  asm("cvt.rzi.s32.f64 %0, %1;" : "=r"(r) : "d"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned to_u32(float v) {
+  unsigned r;
+  asm("cvt.rzi.u32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned to_u32(double v) {
+  unsigned r;
+  asm("cvt.rzi.u32.f64 %0, %1;" : "=r"(r) : "d"(v));
+  return r;
 }
 
 template <typename R>
@@ -63,6 +87,12 @@ __device__ __forceinline__ void store_as(void* ptr, int dtype, int64_t idx, R v)
       ((unsigned short*)ptr)[idx] = h;
       break;
     }
+    case COOT_I32:
+      ((int*)ptr)[idx] = v != v ? 0 : to_s32(v);
+      break;
+    case COOT_U32:
+      ((unsigned*)ptr)[idx] = v != v ? 0u : to_u32(v);
+      break;
     default: {
       unsigned short h;
       const float f = (float)v;
@@ -81,6 +111,13 @@ __device__ __forceinline__ R apply_unary(int op, R a) {
     case U_LOG: return log(a);
     case U_SQRT: return sqrt(a);
     case U_SQUARE: return a * a;
+    case COOT_OP_LOG10: return log10(a);
+    case COOT_OP_SIN: return sin(a);
+    case COOT_OP_COS: return cos(a);
+    case COOT_OP_TAN: return tan(a);
+    case COOT_OP_ASIN: return asin(a);
+    case COOT_OP_ACOS: return acos(a);
+    case COOT_OP_ATAN: return atan(a);
     default: return a;
   }
 }
@@ -91,7 +128,31 @@ __device__ __forceinline__ R apply_binary(int op, R a, R b) {
     case COOT_OP_ADD: return a + b;
     case COOT_OP_SUB: return a - b;
     case COOT_OP_MUL: return a * b;
-    default: return a / b;
+    case COOT_OP_DIV: return a / b;
+    case COOT_OP_LT: return a < b ? (R)1 : (R)0;
+    case COOT_OP_LE: return a <= b ? (R)1 : (R)0;
+    case COOT_OP_GT: return a > b ? (R)1 : (R)0;
+    case COOT_OP_GE: return a >= b ? (R)1 : (R)0;
+    case COOT_OP_EQ: return a == b ? (R)1 : (R)0;
+    case COOT_OP_NE: return a != b ? (R)1 : (R)0;
+    default: return pow(a, b);
+  }
+}
+
+template <>
+__device__ __forceinline__ float apply_binary<float>(int op, float a, float b) {
+  switch (op) {
+    case COOT_OP_ADD: return a + b;
+    case COOT_OP_SUB: return a - b;
+    case COOT_OP_MUL: return a * b;
+    case COOT_OP_DIV: return a / b;
+    case COOT_OP_LT: return a < b ? 1.0f : 0.0f;
+    case COOT_OP_LE: return a <= b ? 1.0f : 0.0f;
+    case COOT_OP_GT: return a > b ? 1.0f : 0.0f;
+    case COOT_OP_GE: return a >= b ? 1.0f : 0.0f;
+    case COOT_OP_EQ: return a == b ? 1.0f : 0.0f;
+    case COOT_OP_NE: return a != b ? 1.0f : 0.0f;
+    default: return powf(a, b);
   }
 }
 
@@ -105,6 +166,13 @@ __device__ __forceinline__ float apply_unary<float>(int op, float a) {
     case U_LOG: return logf(a);
     case U_SQRT: return sqrtf(a);
     case U_SQUARE: return a * a;
+    case COOT_OP_LOG10: return log10f(a);
+    case COOT_OP_SIN: return sinf(a);
+    case COOT_OP_COS: return cosf(a);
+    case COOT_OP_TAN: return tanf(a);
+    case COOT_OP_ASIN: return asinf(a);
+    case COOT_OP_ACOS: return acosf(a);
+    case COOT_OP_ATAN: return atanf(a);
     default: return a;
   }
 }
@@ -153,7 +221,7 @@ __global__ void __launch_bounds__(256) node_kernel(int op, int nb, Operand a, Op
   }
 }
 
-int dsize(int dt) { return dt == COOT_F64 ? 8 : (dt == COOT_F32 ? 4 : 2); }
+int dsize(int dt) { return dt == COOT_F64 ? 8 : (dt == COOT_F32 || dt == COOT_I32 || dt == COOT_U32 ? 4 : 2); }
 
 // 1.0 in device memory: the source of device-to-device copies that write a
 // constant result (all() of an empty object) in stream order, also under
@@ -251,7 +319,8 @@ coot_status coot_unfused_eval(const uint8_t* tree, size_t len, const coot_mat* i
       dst_dtype = rdt;
       dst_ld = R;
     }
-    const bool unary = nd.op >= COOT_OP_NEG && nd.op <= COOT_OP_SQUARE;
+    const bool unary = (nd.op >= COOT_OP_NEG && nd.op <= COOT_OP_SQUARE) ||
+                       (nd.op >= COOT_OP_LOG10 && nd.op <= COOT_OP_ATAN);
     Operand a = val[nd.a];
     Operand b = unary ? Operand{nullptr, 1, rdt, 0.0} : val[nd.b];
     auto ok4 = [&](const Operand& o) {

@@ -31,9 +31,13 @@ static int dtype_size(int dt) {
     case COOT_BF16: return 2;
     case COOT_F16: return 2;
     case COOT_F64: return 8;
+    case COOT_I32: return 4;
+    case COOT_U32: return 4;
   }
   return 0;
 }
+
+static bool is_float(int dt) { return dt == COOT_F32 || dt == COOT_BF16 || dt == COOT_F16 || dt == COOT_F64; }
 
 static coot_status check_mat(const coot_mat* m, const char* what) {
   if (m == nullptr) return fail(COOT_ERR_INVALID_ARG, std::string(what) + " is NULL");
@@ -247,8 +251,19 @@ static Launch heuristic(int kind, int n_in, const View& v, const CallInfo* ci = 
   if (kind == KIND_ROWSUM) {
     l.block = 512;
     l.unroll = n_in >= 3 ? 4 : 8;
-  } else if (kind == KIND_COLSUM || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) {
+  } else if (kind == KIND_COLSUM) {
     l.unroll = 4;
+  } else if (kind == KIND_COLSTATS) {
+    // the statistics' accumulators leave room for 8 accesses in flight
+    l.unroll = 8;
+    if (n_in >= 3) {
+      l.block = 128;
+      l.vec = std::min(l.vec, pick_vec(v, 2));
+    }
+  } else if (kind == KIND_ROWSTATS) {
+    l.block = 128;
+    l.unroll = 8;
+    l.vec = std::min(l.vec, pick_vec(v, 2));
   } else {
     l.unroll = n_in >= 3 ? 4 : 8;
   }
@@ -384,6 +399,7 @@ static coot_status run_sum_dim(const Tree& t, const coot_mat* in, int n_in, int 
   } else {
     return fail(COOT_ERR_INVALID_ARG, "dim must be 0 or 1");
   }
+  if (!is_float(out->dtype)) return fail(COOT_ERR_DTYPE, "sums are stored in a floating-point type");
   bool aliased = false;
   s = check_alias(*out, in, n_in, false, &aliased);
   if (s != COOT_OK) return s;
@@ -564,10 +580,12 @@ static coot_status run_stats_dim(const Tree& t, const coot_mat* in, int n_in, in
     sp.b.rows_per_split = rps;
     units = (Cn * S + warps - 1) / warps;
   } else {
+    // about 6 units per SM: small units keep enough row panels in flight
+    // for the statistics' longer per-element work
     const int64_t groups = std::max(1, l.block / 64);
     const int64_t panel = 64LL * l.vec;
     const int64_t n_panels = (R + panel - 1) / panel;
-    const int64_t target = 3 * (int64_t)d.sm_count / 2;
+    const int64_t target = 6 * (int64_t)d.sm_count;
     int64_t C = std::max<int64_t>(1, (target + n_panels - 1) / n_panels);
     if (l.split > 0) C = l.split;
     C = std::min<int64_t>(C, std::max<int64_t>((Cn + groups - 1) / groups, 1));

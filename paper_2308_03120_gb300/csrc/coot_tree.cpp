@@ -39,8 +39,10 @@ static double rdf64(const uint8_t* p) {
   return d;
 }
 
-static bool is_unary(int op) { return op >= COOT_OP_NEG && op <= COOT_OP_SQUARE; }
-static bool is_binary(int op) { return op >= COOT_OP_ADD && op <= COOT_OP_NE; }
+static bool is_unary(int op) {
+  return (op >= COOT_OP_NEG && op <= COOT_OP_SQUARE) || (op >= COOT_OP_LOG10 && op <= COOT_OP_ATAN);
+}
+static bool is_binary(int op) { return op >= COOT_OP_ADD && op <= COOT_OP_POW; }
 
 coot_status parse_tree(const uint8_t* buf, size_t len, Tree* out) {
   if (buf == nullptr) return fail(COOT_ERR_INVALID_ARG, "tree is NULL");
@@ -140,6 +142,14 @@ static std::string tree_function(const Tree& t) {
       case COOT_OP_GE: e = "(" + a + " >= " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
       case COOT_OP_EQ: e = "(" + a + " == " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
       case COOT_OP_NE: e = "(" + a + " != " + b + ") ? (COOT_REAL)1 : (COOT_REAL)0"; break;
+      case COOT_OP_POW: e = std::string(f32 ? "powf(" : "pow(") + a + ", " + b + ")"; break;
+      case COOT_OP_LOG10: e = std::string(f32 ? "log10f(" : "log10(") + a + ")"; break;
+      case COOT_OP_SIN: e = std::string(f32 ? "sinf(" : "sin(") + a + ")"; break;
+      case COOT_OP_COS: e = std::string(f32 ? "cosf(" : "cos(") + a + ")"; break;
+      case COOT_OP_TAN: e = std::string(f32 ? "tanf(" : "tan(") + a + ")"; break;
+      case COOT_OP_ASIN: e = std::string(f32 ? "asinf(" : "asin(") + a + ")"; break;
+      case COOT_OP_ACOS: e = std::string(f32 ? "acosf(" : "acos(") + a + ")"; break;
+      case COOT_OP_ATAN: e = std::string(f32 ? "atanf(" : "atan(") + a + ")"; break;
     }
     s += "  const COOT_REAL t" + std::to_string(k) + " = " + e + ";\n";
   }

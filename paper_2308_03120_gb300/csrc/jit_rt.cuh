@@ -79,6 +79,8 @@ template <> struct coot_st<0> { typedef float T; };
 template <> struct coot_st<1> { typedef coot_u16 T; };
 template <> struct coot_st<2> { typedef coot_u16 T; };
 template <> struct coot_st<3> { typedef double T; };
+template <> struct coot_st<4> { typedef int T; };
+template <> struct coot_st<5> { typedef coot_u32 T; };
 
 template <int S>
 __device__ __forceinline__ COOT_REAL coot_to_real(typename coot_st<S>::T v) {
@@ -92,7 +94,41 @@ __device__ __forceinline__ COOT_REAL coot_to_real(typename coot_st<S>::T v) {
     asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(v));
     return (COOT_REAL)f;
   } else {
+    // FP64 (rounded to nearest for an FP32 tree) and the integers (nearest
+    // FP32, exact up to 2^24; exact in FP64)
     return (COOT_REAL)v;
+  }
+}
+
+// integer storage of a compute-type value: rounded toward zero, saturated
+// to the type's range, NaN -> 0 (the float-to-integer conversion of PTX)
+__device__ __forceinline__ int coot_f2s32(float v) {
+  int r;
+  asm("cvt.rzi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ int coot_f2s32(double v) {
+  int r;
+  asm("cvt.rzi.s32.f64 %0, %1;" : "=r"(r) : "d"(v));
+  return r;
+}
+__device__ __forceinline__ coot_u32 coot_f2u32(float v) {
+  coot_u32 r;
+  asm("cvt.rzi.u32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ coot_u32 coot_f2u32(double v) {
+  coot_u32 r;
+  asm("cvt.rzi.u32.f64 %0, %1;" : "=r"(r) : "d"(v));
+  return r;
+}
+// (the FP64 conversions do not map NaN to 0 by themselves: NaN is tested)
+template <int S>
+__device__ __forceinline__ typename coot_st<S>::T coot_to_int(COOT_REAL v) {
+  if constexpr (S == 4) {
+    return v != v ? 0 : coot_f2s32(v);
+  } else {
+    return v != v ? 0u : coot_f2u32(v);
   }
 }
 
@@ -110,8 +146,10 @@ __device__ __forceinline__ typename coot_st<S>::T coot_from_real(COOT_REAL v) {
     coot_u16 h;
     asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
     return h;
-  } else {
+  } else if constexpr (S == 3) {
     return (double)v;
+  } else {
+    return coot_to_int<S>(v);
   }
 }
 
@@ -119,6 +157,8 @@ template <int S>
 __device__ __forceinline__ typename coot_st<S>::T coot_from_double(double v) {
   if constexpr (S == 3) {
     return v;
+  } else if constexpr (S >= 4) {
+    return coot_from_real<S>((COOT_REAL)v);
   } else {
     float f = (float)v;  // nearest FP32, then nearest storage value
     if constexpr (S == 0) {
@@ -211,7 +251,12 @@ __device__ __forceinline__ COOT_REAL coot_sload(const typename coot_st<S>::T* p)
     uint2 r = coot_ld8(p);
     return coot_to_real<S>(__longlong_as_double(((coot_i64)r.y << 32) | r.x));
   } else if constexpr (sizeof(T) == 4) {
-    return coot_to_real<S>(__uint_as_float(coot_ld4(p)));
+    union {
+      coot_u32 w;
+      T e;
+    } u;
+    u.w = coot_ld4(p);
+    return coot_to_real<S>(u.e);
   } else {
     return coot_to_real<S>(coot_ld2(p));
   }

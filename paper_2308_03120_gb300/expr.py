@@ -10,7 +10,8 @@ evaluates in one fused kernel.  The operators mirror the paper's Table 2:
     x % y                                 element-wise (Schur) product
     x / y, x / k, k / x                   element-wise division
     -x
-and Table 7's element-wise functions exp, log, sqrt, square, plus abs.
+and Table 7's element-wise functions exp, log, sqrt, square, pow (also
+x ** y), log10, sin, cos, tan, asin, acos, atan, plus abs.
 Relational expressions (Table 5's "A < x" inside all/any) build 1/0
 nodes: x < y, x <= y, x > y, x >= y, and eq(x, y), ne(x, y) (Python's ==
 and != keep their usual meaning on expression objects).
@@ -23,8 +24,10 @@ import struct
 
 _OPS = {"x": 0, "c": 1, "neg": 2, "abs": 3, "exp": 4, "log": 5, "sqrt": 6, "square": 7,
         "add": 8, "sub": 9, "mul": 10, "div": 11,
-        "lt": 12, "le": 13, "gt": 14, "ge": 15, "eq": 16, "ne": 17}
-_BINARY = ("add", "sub", "mul", "div", "lt", "le", "gt", "ge", "eq", "ne")
+        "lt": 12, "le": 13, "gt": 14, "ge": 15, "eq": 16, "ne": 17,
+        "pow": 18, "log10": 19, "sin": 20, "cos": 21, "tan": 22, "asin": 23, "acos": 24, "atan": 25}
+_BINARY = ("add", "sub", "mul", "div", "lt", "le", "gt", "ge", "eq", "ne", "pow")
+_UNARY = ("neg", "abs", "exp", "log", "sqrt", "square", "log10", "sin", "cos", "tan", "asin", "acos", "atan")
 
 
 class Expr:
@@ -96,6 +99,12 @@ class Expr:
     def __ge__(self, o):
         return Expr("ge", (self, Expr._wrap(o)))
 
+    def __pow__(self, o):
+        return Expr("pow", (self, Expr._wrap(o)))
+
+    def __rpow__(self, o):
+        return Expr("pow", (Expr._wrap(o), self))
+
     # ---- nested-tuple form and serialisation
     def sexpr(self):
         if self.op == "x":
@@ -146,6 +155,38 @@ def abs_(e):
     return Expr("abs", (Expr._wrap(e),))
 
 
+def pow_(a, b):
+    return Expr("pow", (Expr._wrap(a), Expr._wrap(b)))
+
+
+def log10(e):
+    return Expr("log10", (Expr._wrap(e),))
+
+
+def sin(e):
+    return Expr("sin", (Expr._wrap(e),))
+
+
+def cos(e):
+    return Expr("cos", (Expr._wrap(e),))
+
+
+def tan(e):
+    return Expr("tan", (Expr._wrap(e),))
+
+
+def asin(e):
+    return Expr("asin", (Expr._wrap(e),))
+
+
+def acos(e):
+    return Expr("acos", (Expr._wrap(e),))
+
+
+def atan(e):
+    return Expr("atan", (Expr._wrap(e),))
+
+
 def eq(a, b):
     """1 where a == b, else 0."""
     return Expr("eq", (Expr._wrap(a), Expr._wrap(b)))
@@ -180,7 +221,7 @@ def serialize(sexpr, compute: str = "f32", n_inputs: int | None = None) -> bytes
             rec = (_OPS["x"], int(t[1]), 0, 0.0)
         elif op == "c":
             rec = (_OPS["c"], 0, 0, float(t[1]))
-        elif op in ("neg", "abs", "exp", "log", "sqrt", "square"):
+        elif op in _UNARY:
             rec = (_OPS[op], walk(t[1]), 0, 0.0)
         elif op in _BINARY:
             a = walk(t[1])

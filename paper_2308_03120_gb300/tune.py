@@ -8,6 +8,8 @@ repetitions when asked).  The fastest shape is the tuner's answer; the
 whole table is the data the learned launch-shape model trains on.
 
     python -m paper_2308_03120_gb300.tune            # the matrix workload's four calls
+    python -m paper_2308_03120_gb300.tune stats      # per-dim statistics
+    python -m paper_2308_03120_gb300.tune batched    # batched evaluation
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ import json
 import statistics
 import sys
 
-from . import KIND_BATCHED, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSUM  # noqa: F401
+from . import KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSTATS, KIND_ROWSUM  # noqa: F401
 
 GRIDS = {
     KIND_MAP: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
@@ -25,6 +27,9 @@ GRIDS = {
     KIND_ROWSUM: dict(block=[64, 128, 256, 512], vec=[0], unroll=[2, 4, 8, 16], blocks_per_sm=[0],
                       split=[0, 8, 16, 32, 64]),
     KIND_BATCHED: dict(block=[128, 256, 512], vec=[0], unroll=[1, 2, 4, 8], blocks_per_sm=[0, 2, 4], split=[0]),
+    KIND_COLSTATS: dict(block=[128, 256, 512], vec=[0, 2], unroll=[2, 4, 8], blocks_per_sm=[0], split=[0, 1, 2, 4]),
+    KIND_ROWSTATS: dict(block=[64, 128, 256], vec=[0, 2, 1], unroll=[2, 4, 8], blocks_per_sm=[0],
+                        split=[0, 8, 16, 32]),
 }
 
 
@@ -132,12 +137,37 @@ def _batched_workload(nmat: int = 4096):
                         lambda: coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work))}
 
 
+def _stats_workload(n: int = 8192):
+    """All six statistics of each column / row, of a stored matrix (one
+    input) and of the four-input matrix tree."""
+    import torch
+
+    import paper_2308_03120_gb300 as coot
+    import synth
+    seed = synth.BASE_SEED + 1
+    dev = [torch.from_numpy(synth.uniform_f32(seed + k, n * n, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0))
+           .cuda() for k in range(4)]
+    mats = [coot.Mat(t, n, n, n) for t in dev]
+    ws = coot.Workspace(n)
+    outs = {0: [coot.Mat(torch.empty(n, device="cuda"), 1, n, 1) for _ in range(6)],
+            1: [coot.Mat(torch.empty(n, device="cuda"), n, 1, n) for _ in range(6)]}
+    calls = {}
+    for name, sexpr, ins in (("leaf", synth.LEAF0, mats[:1]), ("tree", synth.MAT_EXPR, mats)):
+        tree = coot.serialize(sexpr)
+        for dim in (0, 1):
+            calls[f"{name}_dim{dim}"] = (KIND_COLSTATS if dim == 0 else KIND_ROWSTATS, len(ins) * n * n * 4,
+                                         lambda t=tree, i=ins, d=dim: coot.coot_stats_dim(t, i, d, 0x3F, outs[d],
+                                                                                          ws=ws))
+    return calls
+
+
 def main(argv=None):
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build
     build.build()
     coot.coot_init(0)
-    calls = _batched_workload() if argv and argv[0] == "batched" else _matrix_workload()
+    which = argv[0] if argv else "matrices"
+    calls = {"batched": _batched_workload, "stats": _stats_workload}.get(which, _matrix_workload)()
     report = {}
     for name, (kind, nbytes, fn) in calls.items():
         fn()
