@@ -253,6 +253,24 @@ coot_status coot_prepare(const uint8_t* tree, size_t tree_len, int kind, const i
  * (any out pointer may be NULL).  Host-only. */
 coot_status coot_last_launch(int* block, int* vec, int* unroll, int64_t* grid, int64_t* split);
 
+/* Canonical form (on by default, per thread): before a call generates its
+ * kernel, its tree is rewritten with exact rules only -- shared
+ * subexpressions merged, unused nodes dropped, constant subtrees of exactly
+ * rounded operations folded in the compute type, sign and identity rules
+ * (-(-x) = x, x + (-y) = x - y, x % 1 = x, ...), scalar multiples by powers
+ * of two >= 1 merged -- and input slots that name the same matrix, or that
+ * the tree does not read, are merged or dropped, so every distinct operand
+ * is read once.  The result is the same value for every input (the
+ * compile-time rewrites of Section 7, at run time).  enable = 0 turns it off
+ * for the calls that follow on this thread (for measurement).  Host-only. */
+coot_status coot_set_canonical(int enable);
+
+/* The canonical form of a tree into out (cap bytes; the full length goes to
+ * *out_len).  Input slots keep their numbers (the merging and dropping of
+ * slots happens per call, where the operands are known).  Host-only. */
+coot_status coot_tree_canonical(const uint8_t* tree, size_t tree_len, uint8_t* out, size_t cap,
+                                size_t* out_len);
+
 /* Validate a serialised tree without a GPU: on success *n_inputs receives
  * the tree's input count, *compute its compute dtype (COOT_F32 or COOT_F64)
  * and *hash a 64-bit FNV-1a digest of the bytes (the kernel-cache key).

@@ -335,6 +335,21 @@ def coot_sum_rows_f32_static(a: Mat, out: Mat, stream=None) -> None:
 
 # ---------------------------------------------------------------- launch shapes
 
+def coot_set_canonical(enable: bool) -> None:
+    """Canonical forms of the trees of the calls that follow on this thread
+    (on by default)."""
+    _abi.call("coot_set_canonical", int(bool(enable)))
+
+
+def coot_tree_canonical(tree: bytes) -> bytes:
+    """The canonical form of a tree (exact rewrites; host-only)."""
+    n = ctypes.c_size_t()
+    _abi.call("coot_tree_canonical", tree, len(tree), None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value)
+    _abi.call("coot_tree_canonical", tree, len(tree), buf, n.value, ctypes.byref(n))
+    return buf.raw[:n.value]
+
+
 def coot_set_launch_config(kind: int, block: int = 0, vec: int = 0, unroll: int = 0, blocks_per_sm: int = 0,
                            split: int = 0) -> None:
     """Launch shape for the kernels of `kind` on this thread (block = 0

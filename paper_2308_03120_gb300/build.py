@@ -26,7 +26,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcoot.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-HOST_SOURCES = ["coot_api.cpp", "coot_tree.cpp", "coot_jit.cpp", "coot_policy.cpp"]
+HOST_SOURCES = ["coot_api.cpp", "coot_tree.cpp", "coot_jit.cpp", "coot_policy.cpp", "coot_canon.cpp"]
 CUDA_SOURCES = ["coot_aot.cu", "coot_static.cu", "coot_mlp.cu"]
 
 
@@ -92,7 +92,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     jobs = []
     for f in HOST_SOURCES:
         obj = os.path.join(BUILD, f + ".o")
-        jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-function", *inc, "-c",
+        jobs.append((["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-Wall", "-Wno-unused-function", *inc, "-c",
                       os.path.join(CSRC, f), "-o", obj], obj))
     obj = os.path.join(BUILD, "jit_rt_embed.o")
     jobs.append((["g++", "-std=c++17", "-O0", "-fPIC", "-c", embed, "-o", obj], obj))

@@ -276,6 +276,11 @@ coot_status coot_unfused_eval(const uint8_t* tree, size_t len, const coot_mat* i
   coot::Tree t;
   coot_status s = coot::parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
+  if (coot::canonical_enabled()) {
+    coot::Tree c;
+    coot::canonicalize(t, nullptr, &c, nullptr, true);
+    t = std::move(c);
+  }
   if (!in || !out || n_in != t.n_inputs) return coot::fail(COOT_ERR_INVALID_ARG, "bad operands");
   const int64_t R = in[0].n_rows, C = in[0].n_cols;
   for (int i = 0; i < n_in; ++i)

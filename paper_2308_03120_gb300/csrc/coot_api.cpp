@@ -65,13 +65,22 @@ static bool same_mat(const coot_mat& a, const coot_mat& b) {
   return a.ptr == b.ptr && a.dtype == b.dtype && a.n_rows == b.n_rows && a.n_cols == b.n_cols && a.ld == b.ld;
 }
 
-// Tree, operand count, operand checks and equal shapes.
-static coot_status check_operands(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, Tree* t) {
-  coot_status s = parse_tree(tree, len, t);
+// Tree, operand count, operand checks and equal shapes, then the call's
+// canonical form: the tree rewritten exactly and the operands it reads,
+// each distinct matrix once.
+struct Operands {
+  Tree t;
+  coot_mat in[COOT_TREE_MAX_INPUTS];
+  int n = 0;
+};
+
+static coot_status check_operands(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, Operands* ops) {
+  Tree t;
+  coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
   if (in == nullptr) return fail(COOT_ERR_INVALID_ARG, "inputs are NULL");
-  if (n_in != t->n_inputs)
-    return fail(COOT_ERR_INVALID_ARG, "tree has " + std::to_string(t->n_inputs) + " inputs, " +
+  if (n_in != t.n_inputs)
+    return fail(COOT_ERR_INVALID_ARG, "tree has " + std::to_string(t.n_inputs) + " inputs, " +
                                           std::to_string(n_in) + " given");
   for (int i = 0; i < n_in; ++i) {
     s = check_mat(&in[i], "input");
@@ -82,6 +91,25 @@ static coot_status check_operands(const uint8_t* tree, size_t len, const coot_ma
                                       ", input 0 is " + std::to_string(in[0].n_rows) + "x" +
                                       std::to_string(in[0].n_cols));
   }
+  if (!canonical_enabled()) {
+    ops->t = std::move(t);
+    for (int i = 0; i < n_in; ++i) ops->in[i] = in[i];
+    ops->n = n_in;
+    return COOT_OK;
+  }
+  int alias[COOT_TREE_MAX_INPUTS];
+  for (int i = 0; i < n_in; ++i) {
+    alias[i] = i;
+    for (int j = 0; j < i; ++j)
+      if (alias[j] == j && in[i].ptr == in[j].ptr && in[i].dtype == in[j].dtype && in[i].ld == in[j].ld) {
+        alias[i] = j;
+        break;
+      }
+  }
+  std::vector<int> kept;
+  canonicalize(t, alias, &ops->t, &kept, false);
+  ops->n = (int)kept.size();
+  for (int k = 0; k < ops->n; ++k) ops->in[k] = in[kept[k]];
   return COOT_OK;
 }
 
@@ -662,12 +690,22 @@ coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int
   return COOT_OK;
 }
 
+// The canonical form of a tree whose input slots are given positionally
+// (no call-time merging), when canonical forms are on.
+static void canonical_in_place(Tree* t) {
+  if (!canonical_enabled()) return;
+  Tree c;
+  canonicalize(*t, nullptr, &c, nullptr, true);
+  *t = std::move(c);
+}
+
 coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_t* dtypes, int out_dtype,
                          unsigned heads, int block, int vec, int unroll) {
   clear_error();
   Tree t;
   coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
+  canonical_in_place(&t);
   if (kind < 0 || kind >= KIND_COUNT || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
   if (block < 64 || block > 1024 || block % 64) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
   if (!(vec == 1 || vec == 2 || vec == 4 || vec == 8) || unroll < 1 || unroll > 16)
@@ -696,6 +734,7 @@ coot_status coot_call_features(const uint8_t* tree, size_t len, int kind, const 
   Tree t;
   coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
+  canonical_in_place(&t);
   if (kind < 0 || kind > 3 || !dtypes || !features || block < 1) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
   CallInfo c;
   c.kind = kind;
@@ -794,47 +833,47 @@ coot_status coot_tree_compile(const uint8_t* tree, size_t len, int kind, int in_
 coot_status coot_expr_eval(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, const coot_mat* out,
                            void* ws, size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
   if (out == nullptr) return fail(COOT_ERR_INVALID_ARG, "output is NULL");
-  return run_map_reduce(t, in, n_in, 0, out, nullptr, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, 0, out, nullptr, ws, ws_bytes, stream);
 }
 
 coot_status coot_expr_reduce(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, unsigned heads,
                              const coot_mat* out, double* out_dev, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
   if (heads & ~COOT_HEAD_MASK) return fail(COOT_ERR_INVALID_ARG, "unknown head bits");
   if (heads == 0 && out == nullptr) return fail(COOT_ERR_INVALID_ARG, "nothing to compute");
-  return run_map_reduce(t, in, n_in, heads, out, out_dev, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, heads, out, out_dev, ws, ws_bytes, stream);
 }
 
 coot_status coot_accu(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
                       size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
-  return run_map_reduce(t, in, n_in, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 coot_status coot_minmax(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
                         size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
-  return run_map_reduce(t, in, n_in, COOT_HEAD_MIN | COOT_HEAD_MAX, nullptr, out_dev, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, COOT_HEAD_MIN | COOT_HEAD_MAX, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 coot_status coot_norm(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int p, double* out_dev,
                       void* ws, size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
   const bool is_vec = in[0].n_rows == 1 || in[0].n_cols == 1 || n_elem(in[0]) == 0;
   unsigned head;
@@ -848,34 +887,34 @@ coot_status coot_norm(const uint8_t* tree, size_t len, const coot_mat* in, int n
   } else {
     return fail(COOT_ERR_INVALID_ARG, "p must be 1, 2, COOT_NORM_INF, COOT_NORM_NEG_INF or COOT_NORM_FRO");
   }
-  return run_map_reduce(t, in, n_in, head, nullptr, out_dev, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, head, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 coot_status coot_sum_dim(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int dim, const coot_mat* out,
                          void* ws, size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
-  return run_sum_dim(t, in, n_in, dim, out, ws, ws_bytes, stream);
+  return run_sum_dim(o.t, o.in, o.n, dim, out, ws, ws_bytes, stream);
 }
 
 coot_status coot_stats_dim(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int dim, unsigned stats,
                            int norm_type, const coot_mat* out, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
-  return run_stats_dim(t, in, n_in, dim, stats, norm_type, out, ws, ws_bytes, stream);
+  return run_stats_dim(o.t, o.in, o.n, dim, stats, norm_type, out, ws, ws_bytes, stream);
 }
 
 coot_status coot_all_any(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,
                          size_t ws_bytes, void* stream) {
   clear_error();
-  Tree t;
-  coot_status s = check_operands(tree, len, in, n_in, &t);
+  Operands o;
+  coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
-  return run_map_reduce(t, in, n_in, COOT_HEAD_ALL | COOT_HEAD_ANY, nullptr, out_dev, ws, ws_bytes, stream);
+  return run_map_reduce(o.t, o.in, o.n, COOT_HEAD_ALL | COOT_HEAD_ANY, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------ batched evaluation
@@ -953,6 +992,7 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   Tree t;
   coot_status s = parse_tree(tree, len, &t);
   if (s != COOT_OK) return s;
+  canonical_in_place(&t);
   if (in_dtypes == nullptr) return fail(COOT_ERR_INVALID_ARG, "in_dtypes is NULL");
   for (int i = 0; i < t.n_inputs; ++i)
     if (dtype_size(in_dtypes[i]) == 0) return fail(COOT_ERR_DTYPE, "unknown input dtype");
@@ -1031,7 +1071,16 @@ coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void
   Tree t;
   s = parse_tree(buf, sizeof buf, &t);
   if (s != COOT_OK) return s;
-  return run_map_reduce(t, m, 2, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
+  if (!canonical_enabled()) return run_map_reduce(t, m, 2, COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
+  // dot(x, x): one operand, read once
+  const int alias[2] = {0, (m[1].ptr == m[0].ptr && m[1].dtype == m[0].dtype && m[1].ld == m[0].ld &&
+                           m[1].n_rows == m[0].n_rows) ? 0 : 1};
+  Tree c;
+  std::vector<int> kept;
+  canonicalize(t, alias, &c, &kept, false);
+  coot_mat mk[2];
+  for (size_t k = 0; k < kept.size(); ++k) mk[k] = m[kept[k]];
+  return run_map_reduce(c, mk, (int)kept.size(), COOT_HEAD_SUM, nullptr, out_dev, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -100,6 +100,20 @@ uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull
 // Device address of a constant 1.0 on the current device (coot_aot.cu).
 coot_status device_one(const double** out);
 
+// ------------------------------------------------------------ canonical form (coot_canon.cpp)
+
+// Whether calls on this thread canonicalise their trees (default on).
+bool canonical_enabled();
+void set_canonical(bool on);
+// The canonical form of `in` (exact rewrites, common subexpressions,
+// dead nodes dropped).  slot_alias (may be null) maps every input slot to
+// the slot holding the same matrix; kept_slots (may be null) receives the
+// original slots the canonical tree reads, in its new slot order (all slots
+// when keep_slots is set).
+void canonicalize(const Tree& in, const int* slot_alias, Tree* out, std::vector<int>* kept_slots, bool keep_slots);
+// The byte form of a tree (coot.h layout).
+std::vector<uint8_t> serialise(const Tree& t);
+
 // ------------------------------------------------------------ learned launch shapes (coot_policy.cpp)
 
 // What the cost model sees of a call.
