@@ -793,6 +793,44 @@ def run_canonical(args):
                                                 "fused_ms_original": round(t_fused[False], 4)}}), flush=True)
 
 
+def run_views(args):
+    """Submatrix views (ld = 8192 > rows): the matrix tree over the 6144 x
+    6144 window starting at (1024, 1024) of the 8192 x 8192 inputs, stored
+    into the same window of the output, and the column / row sums of the
+    stored window.  Algorithmic bytes: the window's elements only."""
+    import torch
+    import paper_2308_03120_gb300 as coot
+    from paper_2308_03120_gb300 import build as _build
+    _build.build()
+    coot.coot_init(0)
+    seed = synth.BASE_SEED + 1
+    dev = [torch.from_numpy(h).cuda() for h in inputs_host(seed)]
+    full = [coot.Mat(t, N, N, N) for t in dev]
+    w0, w1 = N // 8, N - N // 8 - 1
+    mats = [m.submat(w0, w0, w1, w1) for m in full]
+    O1 = coot.Mat(torch.empty(N * N, device="cuda"), N, N, N).submat(w0, w0, w1, w1)
+    n = w1 - w0 + 1
+    col = coot.Mat(torch.empty(n, device="cuda"), 1, n, 1)
+    row = coot.Mat(torch.empty(n, device="cuda"), n, 1, n)
+    ws = coot.Workspace(n)
+    t_expr = coot.serialize(synth.MAT_EXPR)
+    leaf = coot.serialize(synth.LEAF0)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    calls = {}
+    for name, fn, streams in (("expr_eval", lambda: coot.coot_expr_eval(t_expr, mats, O1), 5),
+                              ("sum_dim0", lambda: coot.coot_sum_dim(leaf, [O1], 0, col, ws=ws), 1),
+                              ("sum_dim1", lambda: coot.coot_sum_dim(leaf, [O1], 1, row, ws=ws), 1)):
+        ms = _timed(torch, stream, fn, args.steps, args.warmup)
+        gbs = streams * n * n * 4 / (ms * 1e-3) / 1e9
+        calls[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                       "launch": shape_text(coot.coot_last_launch())}
+    print(json.dumps({"metric": "fused evaluation and sums over submatrix views HBM GB/s", "workload":
+                      f"{n}x{n} window at ({w0}, {w0}) of {N}x{N} fp32 matrices (ld {N})", "unit": "GB/s",
+                      "calls": calls, "peak": peak, "peak_kind": peak_kind,
+                      "l2": "inputs larger than L2, no flush"}), flush=True)
+
+
 def run_learned(args):
     """Learned launch shapes on random trees the model never saw (fresh
     seed): regret against the exhaustive tuner, model and built-in."""
@@ -831,7 +869,7 @@ def main():
     ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
     ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
     ap.add_argument("--workload", default="matrices",
-                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats", "convert", "canonical"],
+                    choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats", "convert", "canonical", "views"],
                     help="matrices is the headline line; the others print their own line")
     args = ap.parse_args()
     if args.kernel_source_hash:
@@ -857,6 +895,8 @@ def main():
         run_convert(args)
     elif args.workload == "canonical":
         run_canonical(args)
+    elif args.workload == "views":
+        run_views(args)
     else:
         run_coot(args)
 

@@ -357,6 +357,23 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_ma
                              unsigned heads, const coot_mat* out, double* out_dev, void* ws,
                              size_t ws_bytes, void* stream);
 
+/* Submatrix views (Table 1: .rows(a, b), .cols(c, d), .submat(p, q, r, s),
+ * .row(i), .col(j)): the view of rows r0..r1 and columns c0..c1, inclusive,
+ * of m, sharing its storage and ld, usable as any input or output.  Bounds
+ * outside m -> COOT_ERR_SHAPE.  Host-only. */
+coot_status coot_submat(const coot_mat* m, int64_t r0, int64_t c0, int64_t r1, int64_t c1,
+                        coot_mat* view);
+
+/* The k-th diagonal of m (Table 1: .diag(k); k > 0 above the main
+ * diagonal, k < 0 below) as a 1 x n view with ld = m->ld + 1.  A diagonal
+ * outside m -> COOT_ERR_SHAPE.  Host-only. */
+coot_status coot_diag(const coot_mat* m, int64_t k, coot_mat* view);
+
+/* Two operands overlap when they share an element: views of one matrix
+ * with the same ld are compared by their row and column ranges (so
+ * out = A.rows(0, 9) with in = A.rows(10, 19) is allowed); other pairs by
+ * the byte ranges they span. */
+
 /* ------------------------------------------------------------------------
  * Statistics along a dimension (Table 6: max/min/sum(A, dim) and the
  * statistics mean/stddev/var(A, dim)), several in ONE pass over the inputs.

@@ -84,6 +84,35 @@ class Mat:
         ptr = t.data_ptr() + self.offset * t.element_size()
         return coot_mat(ptr, _dtype_code(t), 0, self.n_rows, self.n_cols, self.ld)
 
+    # ---- submatrix views (coot_submat / coot_diag; Table 1)
+    def _view(self, v: coot_mat) -> "Mat":
+        es = self.buf.element_size()
+        return Mat(self.buf, v.n_rows, v.n_cols, v.ld, (v.ptr - self.buf.data_ptr()) // es)
+
+    def submat(self, r0: int, c0: int, r1: int, c1: int) -> "Mat":
+        """Rows r0..r1 and columns c0..c1 (inclusive), sharing storage."""
+        src, v = self.c(), coot_mat()
+        _abi.call("coot_submat", ctypes.byref(src), r0, c0, r1, c1, ctypes.byref(v))
+        return self._view(v)
+
+    def rows(self, a: int, b: int) -> "Mat":
+        return self.submat(a, 0, b, self.n_cols - 1)
+
+    def cols(self, c: int, d: int) -> "Mat":
+        return self.submat(0, c, self.n_rows - 1, d)
+
+    def row(self, i: int) -> "Mat":
+        return self.submat(i, 0, i, self.n_cols - 1)
+
+    def col(self, j: int) -> "Mat":
+        return self.submat(0, j, self.n_rows - 1, j)
+
+    def diag(self, k: int = 0) -> "Mat":
+        """The k-th diagonal as a 1 x n view (ld + 1 apart)."""
+        src, v = self.c(), coot_mat()
+        _abi.call("coot_diag", ctypes.byref(src), k, ctypes.byref(v))
+        return self._view(v)
+
 
 def _mats(ms):
     arr = (coot_mat * len(ms))(*[m.c() for m in ms])

@@ -113,18 +113,34 @@ static coot_status check_operands(const uint8_t* tree, size_t len, const coot_ma
   return COOT_OK;
 }
 
+// Whether two matrices share an element.  With the same dtype and ld they
+// are compared as views of one column-major parent (row and column ranges,
+// so disjoint submatrices of one matrix do not overlap); otherwise by their
+// byte ranges, which may report an overlap that is not there.
+static bool overlaps(const coot_mat& a, const coot_mat& b) {
+  if (n_elem(a) == 0 || n_elem(b) == 0) return false;
+  uintptr_t ab, ae, bb, be;
+  byte_range(a, &ab, &ae);
+  byte_range(b, &bb, &be);
+  if (!(ab < be && bb < ae)) return false;
+  if (a.dtype != b.dtype || a.ld != b.ld) return true;
+  const int64_t es = dtype_size(a.dtype);
+  const int64_t diff = (int64_t)((intptr_t)b.ptr - (intptr_t)a.ptr);
+  if (diff % es != 0) return true;
+  const int64_t d = diff / es;  // b's first element from a's, in elements
+  const int64_t col = d >= 0 ? d / a.ld : -((-d + a.ld - 1) / a.ld);  // floor(d / ld)
+  const int64_t row = d - col * a.ld;                                 // 0 <= row < ld
+  if (row + b.n_rows > a.ld) return true;  // b's columns wrap: not a view of a's parent
+  return row < a.n_rows && col < a.n_cols && col + b.n_cols > 0;
+}
+
 // Output aliasing: identical to an input is allowed (and disables the
 // non-coherent load path), any other overlap is an error.
 static coot_status check_alias(const coot_mat& out, const coot_mat* in, int n_in, bool allow_identical, bool* aliased) {
   *aliased = false;
   if (n_elem(out) == 0) return COOT_OK;
-  uintptr_t ob, oe;
-  byte_range(out, &ob, &oe);
   for (int i = 0; i < n_in; ++i) {
-    if (n_elem(in[i]) == 0) continue;
-    uintptr_t ib, ie;
-    byte_range(in[i], &ib, &ie);
-    if (ob < ie && ib < oe) {
+    if (overlaps(out, in[i])) {
       if (allow_identical && same_mat(out, in[i])) {
         *aliased = true;
       } else {
@@ -897,6 +913,37 @@ coot_status coot_sum_dim(const uint8_t* tree, size_t len, const coot_mat* in, in
   coot_status s = check_operands(tree, len, in, n_in, &o);
   if (s != COOT_OK) return s;
   return run_sum_dim(o.t, o.in, o.n, dim, out, ws, ws_bytes, stream);
+}
+
+coot_status coot_submat(const coot_mat* m, int64_t r0, int64_t c0, int64_t r1, int64_t c1, coot_mat* view) {
+  clear_error();
+  coot_status s = check_mat(m, "matrix");
+  if (s != COOT_OK) return s;
+  if (view == nullptr) return fail(COOT_ERR_INVALID_ARG, "view is NULL");
+  if (r0 < 0 || c0 < 0 || r1 < r0 || c1 < c0 || r1 >= m->n_rows || c1 >= m->n_cols)
+    return fail(COOT_ERR_SHAPE, "submatrix bounds outside the matrix");
+  coot_mat v = *m;
+  v.ptr = (char*)m->ptr + (r0 + c0 * m->ld) * dtype_size(m->dtype);
+  v.n_rows = r1 - r0 + 1;
+  v.n_cols = c1 - c0 + 1;
+  *view = v;
+  return COOT_OK;
+}
+
+coot_status coot_diag(const coot_mat* m, int64_t k, coot_mat* view) {
+  clear_error();
+  coot_status s = check_mat(m, "matrix");
+  if (s != COOT_OK) return s;
+  if (view == nullptr) return fail(COOT_ERR_INVALID_ARG, "view is NULL");
+  const int64_t r0 = k < 0 ? -k : 0, c0 = k > 0 ? k : 0;
+  if (r0 >= m->n_rows || c0 >= m->n_cols) return fail(COOT_ERR_SHAPE, "diagonal outside the matrix");
+  coot_mat v = *m;
+  v.ptr = (char*)m->ptr + (r0 + c0 * m->ld) * dtype_size(m->dtype);
+  v.n_rows = 1;
+  v.n_cols = std::min(m->n_rows - r0, m->n_cols - c0);
+  v.ld = m->ld + 1;  // element j of the diagonal is (r0 + j, c0 + j)
+  *view = v;
+  return COOT_OK;
 }
 
 coot_status coot_stats_dim(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, int dim, unsigned stats,

@@ -34,20 +34,38 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
 #endif
       }
     } else {
-      // the ragged end of a column, one element at a time
+      // the ragged end of a column: whole vectors where they fit (a
+      // column of a strided view ends in one of these every time), then
+      // single elements
 #pragma unroll 1
       for (int k = 0; k < COOT_UNROLL; ++k) {
-#pragma unroll 1
-        for (int v = 0; v < COOT_VEC; ++v) {
-          const coot_i64 row = r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC + v;
-          if (row < p.n_rows) {
-            COOT_REAL x[4];
-            coot_load_one(p, j, row, x);
-            const COOT_REAL y = coot_f(x);
-            acc.add(y);
+        const coot_i64 row0 = r0 + ((coot_i64)k * COOT_BLOCK + threadIdx.x) * COOT_VEC;
+        if (row0 + COOT_VEC <= p.n_rows) {
+          COOT_REAL xv[4][COOT_VEC];
+          coot_load_vec(p, j, row0, xv);
+          COOT_REAL y[COOT_VEC];
+#pragma unroll
+          for (int v = 0; v < COOT_VEC; ++v) {
+            const COOT_REAL x[4] = {xv[0][v], xv[1][v], xv[2][v], xv[3][v]};
+            y[v] = coot_f(x);
+          }
+          acc.add_vec<COOT_VEC>(y);
 #if COOT_STORE
-            coot_sstore<COOT_TO>((TO*)p.out + (j * p.ld_out + row), y);
+          coot_vstore<COOT_TO, COOT_VEC>((TO*)p.out + (j * p.ld_out + row0), y);
 #endif
+        } else {
+#pragma unroll 1
+          for (int v = 0; v < COOT_VEC; ++v) {
+            const coot_i64 row = row0 + v;
+            if (row < p.n_rows) {
+              COOT_REAL x[4];
+              coot_load_one(p, j, row, x);
+              const COOT_REAL y = coot_f(x);
+              acc.add(y);
+#if COOT_STORE
+              coot_sstore<COOT_TO>((TO*)p.out + (j * p.ld_out + row), y);
+#endif
+            }
           }
         }
       }

@@ -478,6 +478,67 @@ __device__ __forceinline__ COOT_REAL coot_pairwise(const COOT_REAL* y, int what)
   return t[0];
 }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+//
+// sm_100-family FP32 pair instructions (add / sub / mul .rn.f32x2) carry two
+// independent lanes in one 64-bit register and one instruction; with the
+// explicit rounding mode they are never contracted into FMAs, so TwoSum keeps
+// its exactness lane by lane.  They halve the instruction count of the
+// per-element sums that otherwise make 2-byte inputs issue-bound.
+#if !COOT_REAL_F64
+typedef coot_u64 coot_f2;
+__device__ __forceinline__ coot_f2 coot_pack(float a, float b) {
+  coot_f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void coot_unpack(coot_f2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ coot_f2 coot_add2(coot_f2 a, coot_f2 b) {
+  coot_f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ coot_f2 coot_sub2(coot_f2 a, coot_f2 b) {
+  coot_f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ coot_f2 coot_mul2(coot_f2 a, coot_f2 b) {
+  coot_f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// two TwoSums, one per lane
+__device__ __forceinline__ void coot_two_sum2(coot_f2& s, coot_f2& c, coot_f2 x) {
+  const coot_f2 t = coot_add2(s, x);
+  const coot_f2 bp = coot_sub2(t, s);
+  const coot_f2 e = coot_add2(coot_sub2(s, coot_sub2(t, bp)), coot_sub2(x, bp));
+  s = t;
+  c = coot_add2(c, e);
+}
+// Pairwise sum of V (even) values, what = 1: their squares (each rounded),
+// 2: their magnitudes; lanes hold the even and odd elements, added in a tree
+// of depth log2(V / 2), then the two lanes.
+template <int V>
+__device__ __forceinline__ float coot_pairwise2(const float* y, int what) {
+  coot_f2 t[V / 2];
+#pragma unroll
+  for (int v = 0; v < V / 2; ++v) {
+    const coot_f2 p = coot_pack(y[2 * v], y[2 * v + 1]);
+    t[v] = what == 1 ? coot_mul2(p, p) : (p & 0x7fffffff7fffffffull);
+  }
+#pragma unroll
+  for (int w = 1; w < V / 2; w *= 2)
+#pragma unroll
+    for (int v = 0; v + w < V / 2; v += 2 * w) t[v] = coot_add2(t[v], t[v + w]);
+  float a, b;
+  coot_unpack(t[0], a, b);
+  return a + b;
+}
+#endif
+
 // ---------------------------------------------------------------- accumulators
 
 #ifndef COOT_HEADS
@@ -502,8 +563,14 @@ struct coot_acc {
   COOT_REAL mn, mx;  // min, max
   COOT_REAL mna, mxa;  // min, max magnitude
   COOT_REAL alz, anz;  // all: smallest nonzero indicator; any: largest
+#if !COOT_REAL_F64
+  coot_f2 s2, sc2;  // the sum of vectors, two lanes (even and odd elements)
+#endif
 
   __device__ __forceinline__ void init() {
+#if !COOT_REAL_F64
+    s2 = sc2 = 0ull;
+#endif
     s = sc = q = qc = a = ac = (COOT_REAL)0;
     mn = mna = alz = (COOT_REAL)COOT_INF_F;
     mx = anz = -(COOT_REAL)COOT_INF_F;
@@ -528,11 +595,27 @@ struct coot_acc {
   // element by element.
   template <int V>
   __device__ __forceinline__ void add_vec(const COOT_REAL* y) {
-    if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
+#if !COOT_REAL_F64
+    constexpr bool packed = V % 2 == 0;
+#else
+    constexpr bool packed = false;
+#endif
+    if constexpr (packed) {
+#if !COOT_REAL_F64
+      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) {
+#pragma unroll
+        for (int v = 0; v < V / 2; ++v) coot_two_sum2(s2, sc2, coot_pack(y[2 * v], y[2 * v + 1]));
+      }
+      if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
+      if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
+#endif
+    } else {
+      if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
+      if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
+    }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, y[v]);
+      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0 && !packed) coot_two_sum(s, sc, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
       if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
@@ -546,7 +629,21 @@ struct coot_acc {
   // normalised; extrema as (value, 0))
   __device__ __forceinline__ void values(COOT_REAL* h, COOT_REAL* l) const {
     int k = 0;
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) { coot_dw_norm(s, sc, h[k], l[k]); ++k; }
+    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) {
+      coot_dw_norm(s, sc, h[k], l[k]);
+#if !COOT_REAL_F64
+      // the two packed lanes, each an exact (sum, compensation) pair
+      float sa, sb, ca, cb;
+      coot_unpack(s2, sa, sb);
+      coot_unpack(sc2, ca, cb);
+      COOT_REAL ha, la, hb, lb;
+      coot_dw_norm(sa, ca, ha, la);
+      coot_dw_norm(sb, cb, hb, lb);
+      coot_dw_add(h[k], l[k], ha, la);
+      coot_dw_add(h[k], l[k], hb, lb);
+#endif
+      ++k;
+    }
     if constexpr ((COOT_HEADS & COOT_HEAD_SUMSQ) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
     if constexpr ((COOT_HEADS & COOT_HEAD_NORM2) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
     if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) { coot_dw_norm(a, ac, h[k], l[k]); ++k; }

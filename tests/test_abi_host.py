@@ -243,3 +243,32 @@ def test_workspace_size_grows_with_rows():
     b = coot.coot_workspace_size(1 << 20)
     assert 65536 < a < b
     assert b >= 64 * (1 << 20) * 8
+
+
+def test_views_of_one_matrix_alias_by_rows_and_columns():
+    """Disjoint submatrices of one parent (same ld) pass the alias check (the
+    call then stops at the uninitialised device); overlapping ones fail."""
+    t = serialize(("mul", synth.C(2.0), synth.X(0)))
+    parent = _fake(1000, 300, ptr=1 << 24)
+    top, bottom, mid = (_abi.coot_mat() for _ in range(3))
+    L = _abi.lib()
+    assert L.coot_submat(ctypes.byref(parent), 0, 0, 499, 299, ctypes.byref(top)) == 0
+    assert L.coot_submat(ctypes.byref(parent), 500, 0, 999, 299, ctypes.byref(bottom)) == 0
+    assert L.coot_submat(ctypes.byref(parent), 250, 0, 749, 299, ctypes.byref(mid)) == 0
+    assert (top.ld, bottom.ld, bottom.ptr - parent.ptr) == (1000, 1000, 500 * 4)
+    ins = (_abi.coot_mat * 1)(bottom)
+    st, _ = _call("coot_expr_eval", t, len(t), ins, 1, ctypes.byref(top), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_NOT_INIT"
+    st, _ = _call("coot_expr_eval", t, len(t), ins, 1, ctypes.byref(mid), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_ALIAS"
+    # columns 0..9 against columns 10..19 of the same rows: disjoint
+    a, b = _abi.coot_mat(), _abi.coot_mat()
+    L.coot_submat(ctypes.byref(parent), 0, 0, 999, 9, ctypes.byref(a))
+    L.coot_submat(ctypes.byref(parent), 0, 10, 999, 19, ctypes.byref(b))
+    st, _ = _call("coot_expr_eval", t, len(t), (_abi.coot_mat * 1)(a), 1, ctypes.byref(b), None, 0, None)
+    assert _abi.STATUS[st] == "COOT_ERR_NOT_INIT"
+    # out of bounds
+    assert L.coot_submat(ctypes.byref(parent), 0, 0, 1000, 0, ctypes.byref(a)) == 3   # COOT_ERR_SHAPE
+    d = _abi.coot_mat()
+    assert L.coot_diag(ctypes.byref(parent), -2, ctypes.byref(d)) == 0
+    assert (d.n_rows, d.n_cols, d.ld, d.ptr - parent.ptr) == (1, 300, 1001, 2 * 4)
