@@ -94,12 +94,16 @@ def committed_traffic(call, shape):
             digest = line.split()[-1]
     if digest != kernel_source_hash():
         return None, "kernel sources changed since the ncu traffic capture"
+    header = None
     for line in text.splitlines():
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 8 and cells[0] == call:
-            if cells[7] != shape:
-                return None, f"launch shape changed since the ncu traffic capture ({cells[7]} -> {shape})"
-            return int(cells[4]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 8192 x 8192"
+        if cells and cells[0] == "call":
+            header = cells
+        elif header and len(cells) == len(header) and cells[0] == call:
+            row = dict(zip(header, cells))
+            if row["launch"] != shape:
+                return None, f"launch shape changed since the ncu traffic capture ({row['launch']} -> {shape})"
+            return int(row["traffic (B)"]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 8192 x 8192"
     return None, f"no traffic row for {call}"
 
 
