@@ -22,7 +22,7 @@ from . import KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE, K
 
 GRIDS = {
     KIND_MAP: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
-    KIND_REDUCE: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
+    KIND_REDUCE: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8, 16], blocks_per_sm=[0], split=[0]),
     KIND_COLSUM: dict(block=[128, 256, 512], vec=[0], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0, 1, 2, 4]),
     KIND_ROWSUM: dict(block=[64, 128, 256, 512], vec=[0], unroll=[2, 4, 8, 16], blocks_per_sm=[0],
                       split=[0, 8, 16, 32, 64]),
@@ -161,13 +161,38 @@ def _stats_workload(n: int = 8192):
     return calls
 
 
+def _precision_workload(n: int = 1 << 28):
+    """The precision workload's calls on BF16 and FP16 vectors of 2^28
+    (signed lognormal values): accu + norm2 of x in one pass and dot(x, z)."""
+    import numpy as np
+    import torch
+
+    import paper_2308_03120_gb300 as coot
+    import synth
+    ws = coot.Workspace(1)
+    res = torch.empty(3, dtype=torch.float64, device="cuda")
+    leaf = coot.serialize(synth.LEAF0)
+    calls = {}
+    for dt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        hx, _ = synth.lognormal_signed(synth.BASE_SEED + 2, n, dt)
+        hz, _ = synth.lognormal_signed(synth.BASE_SEED + 3, n, dt)
+        x = torch.from_numpy(hx.view(np.int16)).view(tdt).cuda()
+        z = torch.from_numpy(hz.view(np.int16)).view(tdt).cuda()
+        X, Z = coot.Mat(x, n, 1, n), coot.Mat(z, n, 1, n)
+        calls[f"{dt}_accu_norm2"] = (KIND_REDUCE, 2 * n, lambda X=X: coot.coot_expr_reduce(
+            leaf, [X], coot.HEAD_SUM | coot.HEAD_NORM2, out_dev=res[0:2], ws=ws))
+        calls[f"{dt}_dot"] = (KIND_REDUCE, 4 * n, lambda X=X, Z=Z: coot.coot_dot(X, Z, out_dev=res[2:3], ws=ws))
+    return calls
+
+
 def main(argv=None):
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build
     build.build()
     coot.coot_init(0)
     which = argv[0] if argv else "matrices"
-    calls = {"batched": _batched_workload, "stats": _stats_workload}.get(which, _matrix_workload)()
+    calls = {"batched": _batched_workload, "stats": _stats_workload,
+             "precision": _precision_workload}.get(which, _matrix_workload)()
     report = {}
     for name, (kind, nbytes, fn) in calls.items():
         fn()
