@@ -374,6 +374,13 @@ coot_status coot_diag(const coot_mat* m, int64_t k, coot_mat* view);
  * out = A.rows(0, 9) with in = A.rows(10, 19) is allowed); other pairs by
  * the byte ranges they span. */
 
+/* The status word of the kernels' bounded waits on this device, then reset
+ * to 0: COOT_OK, or COOT_ERR_TIMEOUT when a wait gave up (the kernel then
+ * stopped early; its outputs are incomplete).  Waits on the device
+ * (mbarriers of the TMA-staged batched kernel) are bounded at about a
+ * second.  Synchronises with the device. */
+coot_status coot_device_status(int* status);
+
 /* ------------------------------------------------------------------------
  * Statistics along a dimension (Table 6: max/min/sum(A, dim) and the
  * statistics mean/stddev/var(A, dim)), several in ONE pass over the inputs.
@@ -408,7 +415,11 @@ coot_status coot_stats_dim(const uint8_t* tree, size_t tree_len, const coot_mat*
  * The paper notes that small matrices leave most of a GPU idle (Section 3)
  * and plans a Cube type for collections of matrices (Section 6); here a
  * persistent kernel walks a work list that covers every matrix, so a batch
- * costs one launch (and can be replayed as one CUDA-graph node).
+ * costs one launch (and can be replayed as one CUDA-graph node).  A work
+ * unit is whole columns of one matrix, about 2048 elements.  When two units
+ * of every input fit in shared memory, each block stages the next dense
+ * unit's inputs with bulk asynchronous copies (TMA, cp.async.bulk) while it
+ * computes the current one; its waits are bounded (coot_device_status).
  * ---------------------------------------------------------------------- */
 
 /* One matrix of a batch (device pointers; 8-byte fields).  Every matrix of

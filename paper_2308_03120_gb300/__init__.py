@@ -333,6 +333,8 @@ def batch_item(ins, out: Mat | None = None, colsum: Mat | None = None) -> _abi.c
     else:
         it.ld_colsum = 1
     it.n_rows, it.n_cols = r, c
+    # the item holds raw pointers: keep the storage alive with it
+    it._keep = [m.buf for m in ins] + [m.buf for m in (out, colsum) if m is not None]
     return it
 
 
@@ -345,7 +347,10 @@ def coot_batch_plan(items, n_inputs: int, device="cuda"):
     _abi.call("coot_batch_plan_size", arr, len(items), ctypes.byref(nbytes), ctypes.byref(n_work))
     host = torch.empty(max(nbytes.value, 16), dtype=torch.uint8)
     _abi.call("coot_batch_plan_build", arr, len(items), n_inputs, ctypes.c_void_p(host.data_ptr()), nbytes.value)
-    return host.to(device), len(items), n_work.value
+    plan = host.to(device)
+    # the plan holds the items' raw pointers: it keeps their storage alive
+    plan._keep = [getattr(it, "_keep", None) for it in items]
+    return plan, len(items), n_work.value
 
 
 def coot_expr_eval_batched(tree: bytes, in_dtypes, out_dtype: int, colsum_dtype: int, plan, n_items: int,

@@ -228,6 +228,10 @@ int dsize(int dt) { return dt == COOT_F64 ? 8 : (dt == COOT_F32 || dt == COOT_I3
 // graph capture.
 __device__ const double g_one = 1.0;
 
+// Status word of the kernels' bounded waits (0, or the coot_status of a
+// wait that gave up).
+__device__ unsigned g_status = 0;
+
 }  // namespace
 
 namespace coot {
@@ -250,7 +254,41 @@ coot_status device_one(const double** out) {
   return COOT_OK;
 }
 
+coot_status device_status_word(unsigned** out) {
+  static std::mutex mu;
+  static unsigned* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return fail(COOT_ERR_CUDA, "no current device");
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_status);
+    if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    addr[dev] = static_cast<unsigned*>(p);
+  }
+  *out = addr[dev];
+  return COOT_OK;
+}
+
 }  // namespace coot
+
+extern "C" coot_status coot_device_status(int* status) {
+  coot::clear_error();
+  if (status == nullptr) return coot::fail(COOT_ERR_INVALID_ARG, "status is NULL");
+  unsigned* word = nullptr;
+  coot_status s = coot::device_status_word(&word);
+  if (s != COOT_OK) return s;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpy(&v, word, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    const unsigned zero = 0;
+    e = cudaMemcpy(word, &zero, sizeof zero, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return coot::fail(COOT_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  *status = (int)v;
+  return COOT_OK;
+}
 
 extern "C" {
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -333,7 +334,7 @@ static void fill_io(coot_params_host* p, const View& v, int n_in) {
 }
 
 static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, const Launch& l, coot_params_host* p,
-                          void* stream, void* kernel_params = nullptr) {
+                          void* stream, void* kernel_params = nullptr, size_t dyn_smem = 0) {
   int bps = std::max(1, c->max_blocks_per_sm);
   if (l.blocks_per_sm > 0) bps = std::min(bps, l.blocks_per_sm);
   int64_t grid = (int64_t)device().sm_count * bps;
@@ -341,7 +342,7 @@ static coot_status launch(const Compiled* c, int64_t units, int64_t max_grid, co
   grid = std::min(grid, max_grid);
   grid = std::max<int64_t>(grid, 1);
   void* args[] = {kernel_params ? kernel_params : (void*)p};
-  cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(l.block), args, 0,
+  cudaError_t e = cudaLaunchKernel((const void*)c->kernel, dim3((unsigned)grid), dim3(l.block), args, dyn_smem,
                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   g_last = l;
@@ -807,7 +808,8 @@ static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype
   for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
   spec->out_dtype = out_dtype;
   spec->store = kind == KIND_MAP || kind == KIND_BATCHED;
-  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
+  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS ||
+                 kind == KIND_BATCHED) ? heads : 0;
   spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
   spec->unroll = 2;
   spec->block = 256;
@@ -972,10 +974,10 @@ struct WorkUnit {
 static_assert(sizeof(coot_batch_item) == 14 * 8, "coot_batch_item layout");
 static_assert(sizeof(WorkUnit) == 16, "work unit layout");
 
-// Columns of one matrix in one work unit (one block): about 8192 elements,
-// whole columns, at least one column per warp-slot.
+// Columns of one matrix in one work unit (one block): about
+// COOT_BATCH_UNIT elements, whole columns.
 static int64_t cols_per_unit(int64_t n_rows) {
-  const int64_t target = 8192;
+  const int64_t target = COOT_BATCH_UNIT;
   if (n_rows <= 0) return target;
   int64_t k = std::max<int64_t>(1, target / n_rows);
   // keep col0 * n_rows a multiple of 4 elements, so that a unit of a
@@ -1057,12 +1059,30 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.vec = 4;
   spec.unroll = 2;
   spec.block = 256;
+  // the TMA-staged kernel (one block per SM, two units of inputs in shared
+  // memory) when two units fit: 8192 elements per input per buffer, plus
+  // the unit's values when they cannot overwrite input 0 in place
+  const int real = t.compute == COOT_F64 ? 8 : 4;
+  size_t buf = 0;
+  for (int i = 0; i < t.n_inputs; ++i) buf += (size_t)COOT_BATCH_UNIT * (size_t)dtype_size(in_dtypes[i]);
+  const size_t vals = dtype_size(in_dtypes[0]) == real ? 0 : (size_t)COOT_BATCH_UNIT * (size_t)real;
+  const size_t smem = 2 * buf + vals + 16 + 2 * sizeof(coot_batch_item) + 2 * 16;
+  // blocks per SM: as many as their shared memory allows (228 KB per SM, 1 KB
+  // of it reserved per block), at most 4 (a sweep over units of 1024, 2048,
+  // 4096 and 8192 elements and 1 to 8 blocks per SM chose 2048 x 4)
+  const int tma_blocks = (int)std::max<size_t>(1, std::min<size_t>(4, (228u * 1024u) / (smem + 1024)));
+  const bool tma = smem <= 227u * 1024u;
   Launch l;
+  if (tma) {
+    spec.heads = 1;
+    spec.block = 256;
+    l.blocks_per_sm = tma_blocks;
+  }
   const Launch& o = g_override[KIND_BATCHED];
   if (o.block) {
     spec.block = o.block;
     if (o.unroll) spec.unroll = o.unroll;
-    l.blocks_per_sm = o.blocks_per_sm;
+    if (!tma || (o.blocks_per_sm > 0 && o.blocks_per_sm <= tma_blocks)) l.blocks_per_sm = o.blocks_per_sm;
   }
   l.block = spec.block;
   l.unroll = spec.unroll;
@@ -1076,7 +1096,26 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   p.split = n_items;
   p.n_work = n_work;
   p.rows_per_split = colsum_dtype;
-  return launch(c, n_work, INT32_MAX, l, &p, stream);
+  if (!tma) return launch(c, n_work, INT32_MAX, l, &p, stream);
+  {
+    // the shared memory limit of each TMA kernel, set once
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> set;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = set.find(c->kernel);
+    if (it == set.end() || it->second < smem) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("shared memory size: ") + cudaGetErrorString(e));
+      set[c->kernel] = smem;
+    }
+  }
+  unsigned* status = nullptr;
+  s = device_status_word(&status);
+  if (s != COOT_OK) return s;
+  p.res = (double*)status;
+  const char* f = std::getenv("COOT_FAULT");
+  if (f && std::string(f) == "batched_wait") p.n_cols = 1;  // a staged unit with no copy: its wait runs out
+  return launch(c, n_work, INT32_MAX, l, &p, stream, nullptr, smem);
 }
 
 coot_status coot_dot(const coot_mat* a, const coot_mat* b, double* out_dev, void* ws, size_t ws_bytes, void* stream) {

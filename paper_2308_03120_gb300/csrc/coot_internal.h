@@ -99,6 +99,8 @@ uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull
 
 // Device address of a constant 1.0 on the current device (coot_aot.cu).
 coot_status device_one(const double** out);
+// Device address of the bounded-wait status word (coot_aot.cu).
+coot_status device_status_word(unsigned** out);
 
 // ------------------------------------------------------------ canonical form (coot_canon.cpp)
 
@@ -170,4 +172,6 @@ static_assert(sizeof(coot_stats_params_host) == 8 * 31, "coot_stats_params layou
 #define COOT_WS_PARTIALS_OFF 65536
 #define COOT_WS_MAX_COUNTERS ((COOT_WS_PARTIALS_OFF - COOT_WS_COUNTERS_OFF) / 4)
 #define COOT_MAX_GRID 4096
+// Elements of a batched work unit (the TMA-staged kernel's COOT_UNIT).
+#define COOT_BATCH_UNIT 2048
 #define COOT_MAX_ROW_CHUNKS 64

@@ -17,8 +17,9 @@ struct coot_batch_item_d {
 };
 
 // One unit of the work list: columns [col0, col0 + n_cols) of one matrix,
-// handled by one block; units hold up to about 8K elements, so the cost of
-// reading the unit and its matrix descriptor is spread over many loads.
+// handled by one block; units hold up to about 2K elements (whole columns),
+// so the cost of reading the unit and its matrix descriptor is spread over
+// many loads.
 struct coot_work_d {
   int item;
   int col0;
@@ -112,6 +113,7 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // stride down the rows.
 // at least 1024 threads resident per SM: the per-unit barriers leave
 // latency that only other blocks can hide
+#if !COOT_TMA
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK < 1024 ? 1024 / COOT_BLOCK : 1))
     COOT_ENTRY(const __grid_constant__ coot_params p) {
   __shared__ COOT_REAL stage[COOT_STAGE];
@@ -239,4 +241,278 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK < 1024 ? 10
     }
   }
 }
+#endif  // !COOT_TMA
+
+#if COOT_TMA
+// ---------------------------------------------------------------- TMA-staged variant
+//
+// Up to four blocks per SM.  Thread 0 copies the next dense unit's inputs into
+// shared memory with bulk asynchronous copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier) while the block computes the current
+// unit from the other buffer: two units of inputs are in flight or staged
+// per SM without passing through registers.  A unit qualifies when every
+// operand is dense (its columns are one contiguous run), it holds at most
+// COOT_UNIT elements, and every input run starts on a 16-byte boundary;
+// the run's last bytes beyond a multiple of 16 are read directly.  Other
+// units take the warp-per-column path from global memory.
+//
+// Every wait on an mbarrier is bounded: a wait that gives up records
+// COOT_ERR_TIMEOUT in the status word (p.res) and the block returns.
+#define COOT_UNIT 2048
+template <int I>
+struct coot_in_bytes {
+  static constexpr int B = I < COOT_NIN ? (int)sizeof(typename coot_st<coot_in_code<I>::S>::T) * COOT_UNIT : 0;
+};
+#define COOT_BUF_BYTES (coot_in_bytes<0>::B + coot_in_bytes<1>::B + coot_in_bytes<2>::B + coot_in_bytes<3>::B)
+#define COOT_VALS_IN_PLACE (sizeof(typename coot_st<COOT_TI0>::T) == sizeof(COOT_REAL))
+
+__device__ __forceinline__ unsigned coot_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// bounded wait for phase `parity` of the mbarrier at bar
+__device__ __forceinline__ bool coot_mbar_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it >= 64) __nanosleep(128);
+  }
+  return false;
+}
+
+// input k's slot in a buffer
+template <int I>
+__device__ __forceinline__ int coot_slot_off() {
+  int o = 0;
+  if constexpr (I > 0) o += coot_in_bytes<0>::B;
+  if constexpr (I > 1) o += coot_in_bytes<1>::B;
+  if constexpr (I > 2) o += coot_in_bytes<2>::B;
+  return o;
+}
+
+// Thread 0: read unit u's descriptor into (sit, swk) and, when it
+// qualifies, start the bulk copies of its inputs into buf; swk->pad
+// records whether it did.
+__device__ void coot_issue(const coot_params& p, coot_i64 u, unsigned char* buf, unsigned bar,
+                           coot_batch_item_d* sit, coot_work_d* swk) {
+  const coot_batch_item_d* items = (const coot_batch_item_d*)p.plan;
+  const coot_work_d* work = (const coot_work_d*)(items + p.split);
+  coot_work_d wk = work[u];
+  const coot_batch_item_d it = items[wk.item];
+  const coot_i64 R = it.n_rows, n = (coot_i64)wk.n_cols * R, b0 = (coot_i64)wk.col0 * R;
+  bool ok = n > 0 && n <= COOT_UNIT && (it.out == nullptr || it.ld_out == R);
+  unsigned tx = 0;
+#define COOT_CHECK_IN(I)                                                                    \
+  if constexpr (I < COOT_NIN) {                                                             \
+    typedef typename coot_st<coot_in_code<I>::S>::T T;                                      \
+    const T* src = (const T*)it.in[I] + b0;                                                 \
+    const unsigned bytes16 = (unsigned)(n * (coot_i64)sizeof(T)) & ~15u;                    \
+    ok = ok && it.ld_in[I] == R && ((unsigned long long)src & 15ull) == 0 && bytes16 > 0;   \
+    tx += bytes16;                                                                          \
+  }
+  COOT_CHECK_IN(0)
+  COOT_CHECK_IN(1)
+  COOT_CHECK_IN(2)
+  COOT_CHECK_IN(3)
+#undef COOT_CHECK_IN
+  wk.pad = ok ? 1 : 0;
+  *sit = it;
+  *swk = wk;
+  // p.n_cols == 1 is the status test: the unit is marked staged but no copy
+  // is started, so its wait runs out (nothing is in flight)
+  if (!ok || p.n_cols == 1) return;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+#define COOT_COPY_IN(I)                                                                     \
+  if constexpr (I < COOT_NIN) {                                                             \
+    typedef typename coot_st<coot_in_code<I>::S>::T T;                                      \
+    const T* src = (const T*)it.in[I] + b0;                                                 \
+    const unsigned bytes16 = (unsigned)(n * (coot_i64)sizeof(T)) & ~15u;                    \
+    asm volatile(                                                                           \
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" \
+        ::"r"(coot_smem_addr(buf + coot_slot_off<I>())), "l"(src), "r"(bytes16), "r"(bar)   \
+        : "memory");                                                                        \
+  }
+  COOT_COPY_IN(0)
+  COOT_COPY_IN(1)
+  COOT_COPY_IN(2)
+  COOT_COPY_IN(3)
+#undef COOT_COPY_IN
+}
+
+// VEC consecutive staged elements of every input at element e
+__device__ __forceinline__ void coot_load_staged(const unsigned char* buf, int e, COOT_REAL (&x)[4][COOT_VEC]) {
+#define COOT_LDS(I)                                                                          \
+  if constexpr (I < COOT_NIN) {                                                              \
+    constexpr int S = coot_in_code<I>::S;                                                    \
+    typedef typename coot_st<S>::T T;                                                        \
+    const T* sp = (const T*)(buf + coot_slot_off<I>()) + e;                                  \
+    _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = coot_to_real<S>(sp[v]);   \
+  } else {                                                                                   \
+    _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = (COOT_REAL)0;             \
+  }
+  COOT_LDS(0)
+  COOT_LDS(1)
+  COOT_LDS(2)
+  COOT_LDS(3)
+#undef COOT_LDS
+}
+
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 : 2)) COOT_ENTRY(const __grid_constant__ coot_params p) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  unsigned char* bufs = dsm;                                           // 2 x COOT_BUF_BYTES
+  COOT_REAL* vals_sep = (COOT_REAL*)(dsm + 2 * COOT_BUF_BYTES);         // COOT_UNIT values unless in place
+  unsigned long long* bars = (unsigned long long*)(dsm + 2 * COOT_BUF_BYTES +
+                                                   (COOT_VALS_IN_PLACE ? 0 : COOT_UNIT * sizeof(COOT_REAL)));
+  coot_batch_item_d* sit = (coot_batch_item_d*)(bars + 2);
+  coot_work_d* swk = (coot_work_d*)(sit + 2);
+  typedef typename coot_st<COOT_TO>::T TO;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool sum64 = p.rows_per_split == 3;
+  const unsigned bar0 = coot_smem_addr(bars), bar1 = coot_smem_addr(bars + 1);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (blockIdx.x < p.n_work) coot_issue(p, blockIdx.x, bufs, bar0, sit, swk);
+  }
+  __syncthreads();
+  unsigned phase[2] = {0u, 0u};
+  int b = 0;
+  for (coot_i64 w = blockIdx.x; w < p.n_work; w += gridDim.x, b ^= 1) {
+    // prefetch the next unit into the other buffer: the block finished with
+    // it at the barrier that ended the previous unit
+    if (threadIdx.x == 0 && w + gridDim.x < p.n_work) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      coot_issue(p, w + gridDim.x, bufs + (b ^ 1) * COOT_BUF_BYTES, b ? bar0 : bar1, sit + (b ^ 1), swk + (b ^ 1));
+    }
+    const coot_batch_item_d it = sit[b];
+    const coot_work_d wk = swk[b];
+    const coot_i64 R = it.n_rows;
+    const coot_i64 c0 = wk.col0, nc = wk.n_cols;
+    if (wk.pad) {
+      const unsigned char* buf = bufs + b * COOT_BUF_BYTES;
+      if (!coot_mbar_wait(b ? bar1 : bar0, phase[b])) {
+        if (threadIdx.x == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
+        return;
+      }
+      phase[b] ^= 1u;
+      const int ni = (int)(nc * R);
+      const coot_i64 b0 = c0 * R;
+      COOT_REAL* vals = COOT_VALS_IN_PLACE ? (COOT_REAL*)(bufs + b * COOT_BUF_BYTES) : vals_sep;
+      TO* out = it.out ? (TO*)it.out + b0 : (TO*)nullptr;
+      // elements staged for every input
+      int ns = ni;
+#define COOT_NS(I)                                                                           \
+  if constexpr (I < COOT_NIN) {                                                              \
+    constexpr int E = (int)sizeof(typename coot_st<coot_in_code<I>::S>::T);                  \
+    ns = min(ns, (int)(((unsigned)(ni * E) & ~15u) / E));                                    \
+  }
+      COOT_NS(0)
+      COOT_NS(1)
+      COOT_NS(2)
+      COOT_NS(3)
+#undef COOT_NS
+      ns -= ns % COOT_VEC;
+      const bool va = out == nullptr || coot_aligned16<0>(out);
+      for (int e = (int)threadIdx.x * COOT_VEC; e < ns; e += COOT_BLOCK * COOT_VEC) {
+        COOT_REAL xv[4][COOT_VEC];
+        coot_load_staged(buf, e, xv);
+        COOT_REAL y[COOT_VEC];
+#pragma unroll
+        for (int k = 0; k < COOT_VEC; ++k) {
+          const COOT_REAL x[4] = {xv[0][k], xv[1][k], xv[2][k], xv[3][k]};
+          y[k] = coot_f(x);
+        }
+        if (out) {
+          if (va) {
+            coot_vstore<COOT_TO, COOT_VEC>(out + e, y);
+          } else {
+#pragma unroll
+            for (int k = 0; k < COOT_VEC; ++k) out[e + k] = coot_from_real<COOT_TO>(y[k]);
+          }
+        }
+        if (it.colsum) {
+#pragma unroll
+          for (int k = 0; k < COOT_VEC; ++k) vals[e + k] = y[k];
+        }
+      }
+      if (ns < ni) {
+        // the last elements of the run, past the copied multiple of 16 bytes
+        coot_batch_item_d sh = it;
+#define COOT_SHIFT_T(I)                                                                                  \
+  if constexpr (I < COOT_NIN) sh.in[I] = (const typename coot_st<coot_in_code<I>::S>::T*)it.in[I] + b0;
+        COOT_SHIFT_T(0)
+        COOT_SHIFT_T(1)
+        COOT_SHIFT_T(2)
+        COOT_SHIFT_T(3)
+#undef COOT_SHIFT_T
+        for (int e = ns + (int)threadIdx.x; e < ni; e += COOT_BLOCK) {
+          COOT_REAL x[4];
+          coot_load_flat(sh, e, x);
+          const COOT_REAL y = coot_f(x);
+          if (out) out[e] = coot_from_real<COOT_TO>(y);
+          if (it.colsum) vals[e] = y;
+        }
+      }
+      if (it.colsum) {
+        __syncthreads();
+        const int Ri = (int)R, nci = (int)nc;
+        if (Ri >= 32) {
+          for (int cj = warp; cj < nci; cj += COOT_WARPS) {
+            COOT_REAL s = 0, c = 0;
+            for (int r = lane; r < Ri; r += 32) coot_two_sum(s, c, vals[cj * Ri + r]);
+            COOT_REAL vh, vl;
+            coot_dw_norm(s, c, vh, vl);
+            coot_dw_warp_sum(vh, vl);
+            if (lane == 0) coot_store_colsum(it, c0 + cj, vh, vl, sum64);
+          }
+        } else {
+          for (int cj = threadIdx.x; cj < nci; cj += COOT_BLOCK) {
+            COOT_REAL s = 0, c = 0;
+            for (int r = 0; r < Ri; ++r) coot_two_sum(s, c, vals[cj * Ri + r]);
+            COOT_REAL vh, vl;
+            coot_dw_norm(s, c, vh, vl);
+            coot_store_colsum(it, c0 + cj, vh, vl, sum64);
+          }
+        }
+      }
+    } else {
+      // strided, large or unaligned units: a warp per column from global memory
+      for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
+        const coot_i64 j = c0 + cj;
+        COOT_REAL s = 0, c = 0;
+        for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
+          COOT_REAL xv[COOT_UNROLL][4];
+#pragma unroll
+          for (int q = 0; q < COOT_UNROLL; ++q) {
+            const coot_i64 r = r0 + 32 * q + lane;
+            if (r < R) coot_load_item(it, j, r, xv[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < COOT_UNROLL; ++q) {
+            const coot_i64 r = r0 + 32 * q + lane;
+            if (r < R) {
+              const COOT_REAL y = coot_f(xv[q]);
+              if (it.out) ((TO*)it.out)[j * it.ld_out + r] = coot_from_real<COOT_TO>(y);
+              coot_two_sum(s, c, y);
+            }
+          }
+        }
+        if (it.colsum) {
+          COOT_REAL vh, vl;
+          coot_dw_norm(s, c, vh, vl);
+          coot_dw_warp_sum(vh, vl);
+          if (lane == 0) coot_store_colsum(it, j, vh, vl, sum64);
+        }
+      }
+    }
+    __syncthreads();  // buffer b and (sit, swk)[b] are free; the prefetch's descriptor is visible
+  }
+}
+#endif  // COOT_TMA
 #endif

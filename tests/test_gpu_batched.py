@@ -1,5 +1,6 @@
 """GPU parity of the batched evaluation (many small matrices of uneven
 shapes in one launch) against the FP64 oracle, matrix by matrix."""
+import ctypes
 import math
 
 import numpy as np
@@ -140,3 +141,85 @@ def test_config_size_batch_sampled():
     pick = sorted(set(np.linspace(0, n - 1, 64).astype(int).tolist()))
     check_batch(tree, [shapes[k] for k in pick], [hosts[k] for k in pick], [outs[k] for k in pick],
                 [sums[k] for k in pick], 3)
+
+
+def test_batch_paths_bf16_four_inputs_and_misaligned():
+    """BF16 inputs (staged, values kept apart from the 2-byte inputs), four
+    FP32 inputs (two units do not fit in shared memory: the register path)
+    and matrices that start off a 16-byte boundary (the global path)."""
+    shapes = [(r, 1 + (r * 7) % 40) for r in (1, 3, 17, 32, 100, 257, 511)]
+    # BF16 (the device tensors stay referenced in `keep`: the items hold
+    # raw pointers)
+    hosts, items, outs, sums, keep = [], [], [], [], []
+    for k, (r, c) in enumerate(shapes):
+        ins = []
+        for s in range(3):
+            x = (synth.uniform_f32(800 + 7 * k + s, r * c) * np.float32(4.0)).astype(np.float32)
+            bits = (x.view(np.uint32) >> np.uint32(16)).astype(np.uint16)   # truncate to BF16 bits
+            ins.append(synth.as_mat(bits, "bf16", r, c))
+        hosts.append(ins)
+        dev = [coot.Mat(torch.from_numpy(h.buf.view(np.int16).copy()).view(torch.bfloat16).cuda(), r, c, r)
+               for h in ins]
+        out = torch.full((r * c,), float("nan"), device="cuda")
+        cs = torch.full((c,), float("nan"), device="cuda")
+        items.append(coot.batch_item(dev, coot.Mat(out, r, c, r), coot.Mat(cs, 1, c, 1)))
+        keep.append(dev)
+        outs.append(out)
+        sums.append(cs)
+    tree = serialize(synth.BATCH_EXPR)
+    plan, n_items, n_work = coot.coot_batch_plan(items, 3)
+    coot.coot_expr_eval_batched(tree, [1, 1, 1], 0, 0, plan, n_items, n_work)
+    torch.cuda.synchronize()
+    check_batch(tree, shapes, hosts, outs, sums, 3)
+    # four FP32 inputs
+    tree4 = serialize(("add", synth.BATCH_EXPR, ("mul", synth.X(3), synth.X(3))))
+    hosts, items, outs, sums, bufs = make_batch(shapes, 810, 4)
+    plan, n_items, n_work = coot.coot_batch_plan(items, 4)
+    coot.coot_expr_eval_batched(tree4, [0, 0, 0, 0], 0, 0, plan, n_items, n_work)
+    torch.cuda.synchronize()
+    check_batch(tree4, shapes, hosts, outs, sums, 4)
+    # operands one element off a 16-byte boundary
+    hosts, items, outs, sums = [], [], [], []
+    for k, (r, c) in enumerate(shapes):
+        ins = [synth.as_mat(synth.uniform_f32(820 + 7 * k + s, r * c), "f32", r, c) for s in range(3)]
+        hosts.append(ins)
+        dev = [coot.Mat(torch.cat([torch.zeros(1), torch.from_numpy(h.buf)]).cuda(), r, c, r, 1) for h in ins]
+        out = torch.full((r * c + 1,), float("nan"), device="cuda")
+        cs = torch.full((c,), float("nan"), device="cuda")
+        items.append(coot.batch_item(dev, coot.Mat(out, r, c, r, 1), coot.Mat(cs, 1, c, 1)))
+        keep.append(dev)
+        outs.append(out[1:])
+        sums.append(cs)
+    plan, n_items, n_work = coot.coot_batch_plan(items, 3)
+    coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work)
+    torch.cuda.synchronize()
+    check_batch(tree, shapes, hosts, outs, sums, 3)
+
+
+def test_bounded_wait_reports_a_timeout(monkeypatch):
+    """A staged unit whose copy is never started (the status test hook):
+    every wait gives up after about a second, the kernel records
+    COOT_ERR_TIMEOUT, and the next batch runs normally."""
+    shapes = [(64, 8)] * 400
+    tree = serialize(synth.BATCH_EXPR)
+    hosts, items, outs, sums, bufs = make_batch(shapes, 830, 3)
+    plan, n_items, n_work = coot.coot_batch_plan(items, 3)
+    coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work)   # compile, status clean
+    torch.cuda.synchronize()
+    status = ctypes.c_int(-1)
+    from paper_2308_03120_gb300 import _abi
+    _abi.call("coot_device_status", ctypes.byref(status))
+    assert status.value == 0
+    monkeypatch.setenv("COOT_FAULT", "batched_wait")
+    coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work)
+    torch.cuda.synchronize()
+    _abi.call("coot_device_status", ctypes.byref(status))
+    assert _abi.STATUS[status.value] == "COOT_ERR_TIMEOUT"
+    monkeypatch.delenv("COOT_FAULT")
+    for o in outs:
+        o.fill_(float("nan"))
+    coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work)
+    torch.cuda.synchronize()
+    _abi.call("coot_device_status", ctypes.byref(status))
+    assert status.value == 0
+    check_batch(tree, shapes, hosts, outs, sums, 3)
