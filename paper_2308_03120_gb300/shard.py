@@ -94,3 +94,108 @@ def gpu_local(tree: bytes, ins, ws=None) -> LocalResults:
         coot.coot_sum_dim(tree, ins, 1, coot.Mat(row, r, 1, r), ws=ws)
     return LocalResults(float(res[0]), float(res[1]), float(res[2]), float(res[3]), n,
                         col.cpu().numpy()[:c], row.cpu().numpy()[:r] if c else np.zeros(r))
+
+
+# ---------------------------------------------------------------- statistics along a dim
+
+@dataclass
+class LocalStats:
+    """One rank's statistics over its column block: for every row the
+    block's count, sum, sum of squared deviations from the block's row mean
+    (M2), min and max; for each of the block's columns its six statistics
+    (sum, mean, var, stddev, min, max), which need no exchange."""
+    width: int                 # columns in the block
+    row_sum: np.ndarray
+    row_m2: np.ndarray
+    row_min: np.ndarray
+    row_max: np.ndarray
+    col_stats: np.ndarray      # 6 x width
+
+
+def _chan(n_a, mean_a, m2_a, n_b, mean_b, m2_b):
+    """Merge two sets' (count, mean, M2) (Chan, Golub and LeVeque's pairwise
+    update; exact in real arithmetic)."""
+    n = n_a + n_b
+    delta = mean_b - mean_a
+    mean = mean_a + delta * (n_b / n)
+    m2 = m2_a + m2_b + delta * delta * (n_a * n_b / n)
+    return n, mean, m2
+
+
+def merge_stats(parts, n_rows: int, norm_type: int = 0) -> dict:
+    """Statistics of the whole matrix from its column blocks' LocalStats, in
+    block order: rows merge the blocks' (count, mean, M2) (so the result
+    does not depend on timing; min / max propagate NaN), columns are
+    concatenated."""
+    n, mean, m2 = 0, np.zeros(n_rows), np.zeros(n_rows)
+    lo, hi = np.full(n_rows, np.inf), np.full(n_rows, -np.inf)
+    total = np.zeros(n_rows)
+    with np.errstate(invalid="ignore"):
+        for p in parts:
+            if p.width == 0:
+                continue
+            if n == 0:
+                n, mean, m2 = p.width, p.row_sum / p.width, p.row_m2
+            else:
+                n, mean, m2 = _chan(n, mean, m2, p.width, p.row_sum / p.width, p.row_m2)
+            total = total + p.row_sum
+            lo, hi = np.minimum(lo, p.row_min), np.maximum(hi, p.row_max)
+    d = n - 1 + norm_type
+    with np.errstate(invalid="ignore", divide="ignore"):
+        if n == 0:
+            var = np.full(n_rows, np.nan)
+        elif d == 0:
+            var = np.where(np.isfinite(total), 0.0, np.nan)
+        else:
+            var = np.maximum(m2 / d, 0.0)
+    cols = np.concatenate([np.asarray(p.col_stats, dtype=np.float64).reshape(6, p.width) for p in parts], axis=1)
+    return {"rows": {"sum": total, "mean": mean if n else np.full(n_rows, np.nan), "var": var,
+                     "stddev": np.sqrt(var), "min": lo, "max": hi},
+            "cols": dict(zip(("sum", "mean", "var", "stddev", "min", "max"), cols))}
+
+
+def combine_stats(local: LocalStats, n_rows: int, n_cols: int, norm_type: int = 0, group=None) -> dict:
+    """merge_stats over every rank's LocalStats (collective: each rank's
+    block is gathered, then merged in rank order on every rank)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    widths = [column_block(n_cols, r, world)[1] - column_block(n_cols, r, world)[0] for r in range(world)]
+    width = max(widths)
+    mine = torch.zeros(4 * n_rows + 6 * width, dtype=torch.float64)
+    rows = np.stack([local.row_sum, local.row_m2, local.row_min, local.row_max]).astype(np.float64)
+    mine[:4 * n_rows] = torch.from_numpy(np.ascontiguousarray(rows.ravel()))
+    cols = np.zeros((6, width))
+    cols[:, :local.width] = np.asarray(local.col_stats, dtype=np.float64).reshape(6, local.width)
+    mine[4 * n_rows:] = torch.from_numpy(cols.ravel())
+    gathered = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(gathered, mine, group=group)
+    parts = []
+    for r in range(world):
+        g = gathered[r].numpy()
+        rs = g[:4 * n_rows].reshape(4, n_rows)
+        cs = g[4 * n_rows:].reshape(6, width)[:, :widths[r]]
+        parts.append(LocalStats(widths[r], rs[0], rs[1], rs[2], rs[3], cs))
+    return merge_stats(parts, n_rows, norm_type)
+
+
+def gpu_local_stats(tree: bytes, ins, norm_type: int = 0, ws=None) -> LocalStats:
+    """A rank's LocalStats on its own GPU block through coot_stats_dim (ins:
+    the rank's column blocks as coot Mats on its device)."""
+    import torch
+
+    import paper_2308_03120_gb300 as coot
+    r, c = ins[0].n_rows, ins[0].n_cols
+    rows = [torch.empty(max(r, 1), dtype=torch.float64, device="cuda") for _ in range(4)]
+    if r and c:
+        # sum, var with divisor N (so M2 = var * N), min, max of each row
+        coot.coot_stats_dim(tree, ins, 1, coot.STAT_SUM | coot.STAT_VAR | coot.STAT_MIN | coot.STAT_MAX,
+                            [coot.Mat(t, r, 1, r) for t in rows], norm_type=1, ws=ws)
+    cols = [torch.empty(max(c, 1), dtype=torch.float64, device="cuda") for _ in range(6)]
+    if c and r:
+        coot.coot_stats_dim(tree, ins, 0, 0x3F, [coot.Mat(t, 1, c, 1) for t in cols], norm_type=norm_type, ws=ws)
+    h = [t.cpu().numpy()[:r] for t in rows]
+    col = np.stack([t.cpu().numpy()[:c] for t in cols]) if c else np.zeros((6, 0))
+    if not c:
+        h = [np.zeros(r), np.zeros(r), np.full(r, np.inf), np.full(r, -np.inf)]
+    return LocalStats(c, h[0], h[1] * c, h[2], h[3], col)

@@ -246,3 +246,23 @@ def test_launch_shape_overrides(kind, block, unroll, split):
     finally:
         coot.coot_set_launch_config(kind, 0)
     check_stats(tree, ins, kind - 5, got)
+
+
+def test_column_blocks_merge_to_the_whole():
+    """Three column blocks' statistics computed on the GPU (shard.gpu_local_stats)
+    and merged in block order (shard.merge_stats) equal the oracle over the
+    whole matrix: the per-rank half of a sharded run."""
+    from paper_2308_03120_gb300 import shard
+    r, c = 1001, 103
+    specs = [_f32(r, c), _f32(r, c), _f32(r, c), _f32(r, c, lo=0.0, hi=2.0)]
+    tree, ins, dev = _inputs(synth.MAT_EXPR, specs, 277)
+    parts = []
+    for k in range(3):
+        c0, c1 = shard.column_block(c, k, 3)
+        blocks = [m.cols(c0, c1 - 1) for m in dev]
+        parts.append(shard.gpu_local_stats(tree, blocks))
+    merged = shard.merge_stats(parts, r, 0)
+    for s in NAMES:
+        want_rows = O.stats_dim(tree, ins, 1, s)
+        np.testing.assert_allclose(merged["rows"][s], want_rows, rtol=2e-6, atol=1e-6, err_msg=s)
+        np.testing.assert_allclose(merged["cols"][s], O.stats_dim(tree, ins, 0, s), rtol=2e-6, atol=1e-6, err_msg=s)

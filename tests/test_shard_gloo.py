@@ -106,3 +106,62 @@ def test_column_blocks_cover_every_column_once():
             assert all(blocks[i][1] == blocks[i + 1][0] for i in range(world - 1))
             widths = [b - a for a, b in blocks]
             assert max(widths) - min(widths) <= 1
+
+
+# ---------------------------------------------------------------- sharded statistics
+
+def _oracle_local_stats(tree, mats, rank, world, norm_type):
+    from paper_2308_03120_gb300.shard import LocalStats
+    c0, c1 = column_block(mats[0].n_cols, rank, world)
+    r, w = mats[0].n_rows, c1 - c0
+    blk = [synth.as_mat(m.buf[c0 * m.ld:c1 * m.ld].copy(), m.dtype, r, w, m.ld) for m in mats]
+    if w == 0:
+        return LocalStats(0, np.zeros(r), np.zeros(r), np.full(r, np.inf), np.full(r, -np.inf), np.zeros((6, 0)))
+    st = lambda dim, s, nt=0: O.stats_dim(tree, blk, dim, s, nt)  # noqa: E731
+    cols = np.stack([st(0, s, norm_type) for s in O.STATS])
+    return LocalStats(w, st(1, "sum"), st(1, "var", 1) * w, st(1, "min"), st(1, "max"), cols)
+
+
+def _stats_worker(rank, world, port, shape, seed, norm_type, q):
+    import torch.distributed as dist
+    from paper_2308_03120_gb300.shard import combine_stats
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, c = shape
+        mats = [synth.as_mat(synth.uniform_f32(seed + k, r * c, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
+                             "f32", r, c) for k in range(4)]
+        tree = O.encode(synth.MAT_EXPR)
+        q.put((rank, combine_stats(_oracle_local_stats(tree, mats, rank, world, norm_type), r, c, norm_type)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,shape,norm_type", [(2, (67, 101), 0), (3, (40, 8), 1), (3, (9, 2), 0)])
+def test_sharded_statistics_equal_the_whole(world, shape, norm_type):
+    """Row statistics merge the ranks' (count, mean, M2) in rank order;
+    column statistics are gathered.  Against the oracle over the whole
+    matrix."""
+    seed = 2468
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_stats_worker, args=(r, world, port, shape, seed, norm_type, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    r, c = shape
+    mats = [synth.as_mat(synth.uniform_f32(seed + k, r * c, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
+                         "f32", r, c) for k in range(4)]
+    tree = O.encode(synth.MAT_EXPR)
+    for rank, res in out.items():
+        for s in O.STATS:
+            want_rows = O.stats_dim(tree, mats, 1, s, norm_type)
+            np.testing.assert_allclose(res["rows"][s], want_rows, rtol=1e-12, atol=1e-13, err_msg=s)
+            assert np.array_equal(res["cols"][s], O.stats_dim(tree, mats, 0, s, norm_type)), s
+            assert np.array_equal(res["rows"][s], out[0]["rows"][s])      # every rank agrees
