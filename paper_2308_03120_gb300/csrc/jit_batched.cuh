@@ -344,14 +344,65 @@ __device__ void coot_issue(const coot_params& p, coot_i64 u, unsigned char* buf,
 #undef COOT_COPY_IN
 }
 
+// V consecutive elements of storage S at shared-memory address a (aligned
+// to V * sizeof(T)), one vector access
+template <int S, int V>
+__device__ __forceinline__ void coot_lds_vec(unsigned a, COOT_REAL* x) {
+  typedef typename coot_st<S>::T T;
+  constexpr int B = V * (int)sizeof(T);
+  union {
+    uint4 q[B >= 16 ? B / 16 : 1];
+    uint2 d;
+    coot_u32 w;
+    T e[V];
+  } u;
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i)
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(u.q[i].x), "=r"(u.q[i].y), "=r"(u.q[i].z), "=r"(u.q[i].w) : "r"(a + 16 * i));
+  } else if constexpr (B == 8) {
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(u.d.x), "=r"(u.d.y) : "r"(a));
+  } else if constexpr (B == 4) {
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(u.w) : "r"(a));
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) u.e[v] = ((const T*)__cvta_shared_to_generic(a))[v];
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) x[v] = coot_to_real<S>(u.e[v]);
+}
+
+// V values of the compute type to shared-memory address a (aligned to
+// V * sizeof(COOT_REAL)), 16-byte accesses
+template <int V>
+__device__ __forceinline__ void coot_sts_real(unsigned a, const COOT_REAL* y) {
+  constexpr int B = V * (int)sizeof(COOT_REAL);
+  union {
+    uint4 q[B >= 16 ? B / 16 : 1];
+    COOT_REAL e[V];
+  } u;
+#pragma unroll
+  for (int v = 0; v < V; ++v) u.e[v] = y[v];
+  if constexpr (B >= 16 && B % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i)
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                   :: "r"(a + 16 * i), "r"(u.q[i].x), "r"(u.q[i].y), "r"(u.q[i].z), "r"(u.q[i].w) : "memory");
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) ((COOT_REAL*)__cvta_shared_to_generic(a))[v] = y[v];
+  }
+}
+
 // VEC consecutive staged elements of every input at element e
 __device__ __forceinline__ void coot_load_staged(const unsigned char* buf, int e, COOT_REAL (&x)[4][COOT_VEC]) {
+  const unsigned base = coot_smem_addr(buf);
 #define COOT_LDS(I)                                                                          \
   if constexpr (I < COOT_NIN) {                                                              \
     constexpr int S = coot_in_code<I>::S;                                                    \
     typedef typename coot_st<S>::T T;                                                        \
-    const T* sp = (const T*)(buf + coot_slot_off<I>()) + e;                                  \
-    _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = coot_to_real<S>(sp[v]);   \
+    coot_lds_vec<S, COOT_VEC>(base + coot_slot_off<I>() + e * (unsigned)sizeof(T), x[I]);   \
   } else {                                                                                   \
     _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) x[I][v] = (COOT_REAL)0;             \
   }
@@ -381,7 +432,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
     if (blockIdx.x < p.n_work) coot_issue(p, blockIdx.x, bufs, bar0, sit, swk);
   }
   __syncthreads();
-  unsigned phase[2] = {0u, 0u};
+  unsigned phases = 0u;  // bit s: the parity of buffer s's next phase
   int b = 0;
   for (coot_i64 w = blockIdx.x; w < p.n_work; w += gridDim.x, b ^= 1) {
     // prefetch the next unit into the other buffer: the block finished with
@@ -396,11 +447,11 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
     const coot_i64 c0 = wk.col0, nc = wk.n_cols;
     if (wk.pad) {
       const unsigned char* buf = bufs + b * COOT_BUF_BYTES;
-      if (!coot_mbar_wait(b ? bar1 : bar0, phase[b])) {
+      if (!coot_mbar_wait(b ? bar1 : bar0, (phases >> b) & 1u)) {
         if (threadIdx.x == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
         return;
       }
-      phase[b] ^= 1u;
+      phases ^= 1u << b;
       const int ni = (int)(nc * R);
       const coot_i64 b0 = c0 * R;
       COOT_REAL* vals = COOT_VALS_IN_PLACE ? (COOT_REAL*)(bufs + b * COOT_BUF_BYTES) : vals_sep;
@@ -436,10 +487,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
             for (int k = 0; k < COOT_VEC; ++k) out[e + k] = coot_from_real<COOT_TO>(y[k]);
           }
         }
-        if (it.colsum) {
-#pragma unroll
-          for (int k = 0; k < COOT_VEC; ++k) vals[e + k] = y[k];
-        }
+        if (it.colsum) coot_sts_real<COOT_VEC>(coot_smem_addr(vals + e), y);
       }
       if (ns < ni) {
         // the last elements of the run, past the copied multiple of 16 bytes
