@@ -107,8 +107,8 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // one contiguous run) that fit the stage: every thread streams the run
 // flat, COOT_UNROLL elements per input in flight, writes the values and
 // keeps them in shared memory; the column sums are then taken from shared
-// memory (a warp per column with a double-word shuffle sum for columns of
-// at least 32 rows, a thread per column below that), each in a fixed order.
+// memory (g lanes per column, each adding 8 or more values, then a
+// double-word shuffle sum over the g lanes), each in a fixed order.
 // Other units: warp w of the block takes columns w, w + warps, ...; lanes
 // stride down the rows.
 // at least 1024 threads resident per SM: the per-unit barriers leave
@@ -509,24 +509,42 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
       }
       if (it.colsum) {
         __syncthreads();
+        // g lanes per column, g the largest power of two up to 32 that
+        // leaves each lane 8 or more of the column's values (one lane per
+        // column below 16 rows), 32 / g columns per warp pass.  Lane `sub`
+        // of a column adds rows sub, sub + g, ... in chunks of g rows,
+        // starting at a column-dependent chunk so that the columns of one
+        // pass read different banks (one lane per column: only for even
+        // lengths, odd ones already spread); then the g lanes combine.
         const int Ri = (int)R, nci = (int)nc;
-        if (Ri >= 32) {
-          for (int cj = warp; cj < nci; cj += COOT_WARPS) {
-            COOT_REAL s = 0, c = 0;
-            for (int r = lane; r < Ri; r += 32) coot_two_sum(s, c, vals[cj * Ri + r]);
-            COOT_REAL vh, vl;
-            coot_dw_norm(s, c, vh, vl);
-            coot_dw_warp_sum(vh, vl);
-            if (lane == 0) coot_store_colsum(it, c0 + cj, vh, vl, sum64);
+        int g = 32;
+        while (g > 1 && g * 8 > Ri) g >>= 1;
+        const int cpw = 32 / g, sub = lane & (g - 1);
+        const int nch = (Ri + g - 1) / g;
+        for (int cb = warp * cpw; cb < nci; cb += COOT_WARPS * cpw) {
+          const int jj = cb + lane / g;
+          COOT_REAL s = 0, c = 0;
+          if (jj < nci) {
+            const COOT_REAL* col = vals + jj * Ri;
+            if (g == 32) {
+              for (int r = lane; r < Ri; r += 32) coot_two_sum(s, c, col[r]);
+            } else {
+              int ch = (g > 1 || (Ri & 1) == 0) ? jj % nch : 0;
+              for (int i = 0; i < nch; ++i) {
+                const int r = ch * g + sub;
+                if (r < Ri) coot_two_sum(s, c, col[r]);
+                if (++ch == nch) ch = 0;
+              }
+            }
           }
-        } else {
-          for (int cj = threadIdx.x; cj < nci; cj += COOT_BLOCK) {
-            COOT_REAL s = 0, c = 0;
-            for (int r = 0; r < Ri; ++r) coot_two_sum(s, c, vals[cj * Ri + r]);
-            COOT_REAL vh, vl;
-            coot_dw_norm(s, c, vh, vl);
-            coot_store_colsum(it, c0 + cj, vh, vl, sum64);
+          COOT_REAL vh, vl;
+          coot_dw_norm(s, c, vh, vl);
+          for (int o = g >> 1; o > 0; o >>= 1) {
+            const COOT_REAL yh = __shfl_down_sync(0xffffffffu, vh, o);
+            const COOT_REAL yl = __shfl_down_sync(0xffffffffu, vl, o);
+            coot_dw_add(vh, vl, yh, yl);
           }
+          if (jj < nci && sub == 0) coot_store_colsum(it, c0 + jj, vh, vl, sum64);
         }
       }
     } else {
