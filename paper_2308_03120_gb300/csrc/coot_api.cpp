@@ -808,8 +808,7 @@ static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype
   for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
   spec->out_dtype = out_dtype;
   spec->store = kind == KIND_MAP || kind == KIND_BATCHED;
-  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS ||
-                 kind == KIND_BATCHED) ? heads : 0;
+  spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
   spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
   spec->unroll = 2;
   spec->block = 256;
@@ -1059,30 +1058,26 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.vec = 4;
   spec.unroll = 2;
   spec.block = 256;
-  // the TMA-staged kernel (one block per SM, two units of inputs in shared
-  // memory) when two units fit: 8192 elements per input per buffer, plus
-  // the unit's values when they cannot overwrite input 0 in place
+  // Shared memory: two buffers of COOT_BATCH_UNIT elements per input, plus
+  // the unit's values when they cannot overwrite input 0 in place (at most
+  // 2 x 4 x 2048 x 8 B + 16 KB, always within the 227 KB of a block)
   const int real = t.compute == COOT_F64 ? 8 : 4;
   size_t buf = 0;
   for (int i = 0; i < t.n_inputs; ++i) buf += (size_t)COOT_BATCH_UNIT * (size_t)dtype_size(in_dtypes[i]);
   const size_t vals = dtype_size(in_dtypes[0]) == real ? 0 : (size_t)COOT_BATCH_UNIT * (size_t)real;
   const size_t smem = 2 * buf + vals + 16 + 2 * sizeof(coot_batch_item) + 2 * 16;
+  if (smem > 227u * 1024u) return fail(COOT_ERR_UNSUPPORTED, "batched: two units of the inputs exceed shared memory");
   // blocks per SM: as many as their shared memory allows (228 KB per SM, 1 KB
   // of it reserved per block), at most 4 (a sweep over units of 1024, 2048,
   // 4096 and 8192 elements and 1 to 8 blocks per SM chose 2048 x 4)
-  const int tma_blocks = (int)std::max<size_t>(1, std::min<size_t>(4, (228u * 1024u) / (smem + 1024)));
-  const bool tma = smem <= 227u * 1024u;
+  const int max_blocks = (int)std::max<size_t>(1, std::min<size_t>(4, (228u * 1024u) / (smem + 1024)));
   Launch l;
-  if (tma) {
-    spec.heads = 1;
-    spec.block = 256;
-    l.blocks_per_sm = tma_blocks;
-  }
+  l.blocks_per_sm = max_blocks;
   const Launch& o = g_override[KIND_BATCHED];
   if (o.block) {
     spec.block = o.block;
     if (o.unroll) spec.unroll = o.unroll;
-    if (!tma || (o.blocks_per_sm > 0 && o.blocks_per_sm <= tma_blocks)) l.blocks_per_sm = o.blocks_per_sm;
+    if (o.blocks_per_sm > 0 && o.blocks_per_sm <= max_blocks) l.blocks_per_sm = o.blocks_per_sm;
   }
   l.block = spec.block;
   l.unroll = spec.unroll;
@@ -1096,9 +1091,8 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   p.split = n_items;
   p.n_work = n_work;
   p.rows_per_split = colsum_dtype;
-  if (!tma) return launch(c, n_work, INT32_MAX, l, &p, stream);
   {
-    // the shared memory limit of each TMA kernel, set once
+    // the shared memory limit of each batched kernel, set once
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
     std::lock_guard<std::mutex> lock(mu);

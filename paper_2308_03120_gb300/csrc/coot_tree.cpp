@@ -178,12 +178,12 @@ std::string generate_source(const Tree& t, const KernelSpec& spec) {
                 "#define COOT_TI0 %d\n#define COOT_TI1 %d\n#define COOT_TI2 %d\n#define COOT_TI3 %d\n"
                 "#define COOT_TO %d\n#define COOT_STORE %d\n#define COOT_HEADS %uu\n"
                 "#define COOT_REAL %s\n#define COOT_REAL_F64 %d\n#define COOT_VEC %d\n#define COOT_UNROLL %d\n"
-                "#define COOT_BLOCK %d\n#define COOT_NC %d\n#define COOT_TMA %d\n",
+                "#define COOT_BLOCK %d\n#define COOT_NC %d\n",
                 t.hash, entry_name(spec), spec.kind, t.n_inputs, spec.in_dtype[0], spec.in_dtype[1], spec.in_dtype[2],
                 spec.in_dtype[3], spec.out_dtype, spec.store ? 1 : 0, spec.heads,
                 t.compute == COOT_F32 ? "float" : "double", t.compute == COOT_F32 ? 0 : 1, spec.vec, spec.unroll,
                 spec.block,
-                spec.nc ? 1 : 0, spec.kind == KIND_BATCHED && (spec.heads & 1) ? 1 : 0);
+                spec.nc ? 1 : 0);
   std::string src(pre);
   src += tree_function(t);
   src += coot_jit_rt_source;
