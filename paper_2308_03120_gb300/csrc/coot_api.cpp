@@ -311,6 +311,19 @@ static Launch heuristic(int kind, int n_in, const View& v, const CallInfo* ci = 
     l.vec = std::min(l.vec, pick_vec(v, 2));
   } else {
     l.unroll = n_in >= 3 ? 4 : 8;
+    // Small inputs: fewer elements per thread until the grid covers the
+    // GPU, about 4 blocks per SM for element-wise evaluation and 1.5 for
+    // calls with reduction heads, whose last block combines one partial
+    // per block (sweeps over block, vector width and unroll on a 10^6
+    // vector, each call replayed in a CUDA graph: 3.5 -> 2.6 us for
+    // 2x + 3z, 6.8 -> 5.9 us for accu(x % z)).
+    const bool heads = kind == KIND_REDUCE || (ci != nullptr && ci->heads != 0);
+    const int64_t want = heads ? (int64_t)device().sm_count * 3 / 2 : (int64_t)device().sm_count * 4;
+    auto units = [&](int unroll) {
+      const int64_t tile = (int64_t)l.block * l.vec * unroll;
+      return ((v.n_rows + tile - 1) / tile) * v.n_cols;
+    };
+    while (l.unroll > 1 && units(l.unroll) < want) l.unroll /= 2;
   }
   if (o.block) {
     l.block = o.block;
