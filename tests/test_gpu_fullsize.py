@@ -166,3 +166,106 @@ def test_precision_workload_2_28(dt):
     yb = (yh.view(torch.int16).numpy().view(np.uint16) if dt == "bf16" else yh.numpy())[idx]
     rep = check_elementwise(serialize(synth.AXPY_2X_3Z), ins, synth.as_mat(yb, dt, idx.size, 1))
     print(f"{dt} 2x+3z: {rep}")
+
+
+@pytest.mark.parametrize("sexpr", [synth.LEAF0, synth.MAT_EXPR])
+def test_statistics_workload_8192(sexpr):
+    """All six statistics of every column and every row of the 8192 x 8192
+    inputs (a stored matrix, and the four-input tree), at the launch shapes
+    the benchmark times; 48 sampled columns and 48 sampled rows (the first
+    and last included) are checked against the oracle with the tolerances
+    of the statistics tests."""
+    from tests.test_gpu_stats import NAMES, check_stats
+    seed = synth.BASE_SEED + 1
+    n_in = synth.tree_inputs(sexpr)
+    host = [synth.as_mat(synth.uniform_f32(seed + k, N * N, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
+                         "f32", N, N) for k in range(n_in)]
+    dev = [coot.Mat(torch.from_numpy(h.buf).cuda(), N, N, N) for h in host]
+    tree = serialize(sexpr)
+    ws = coot.Workspace(N)
+    rng = np.random.default_rng(11)
+    for dim in (0, 1):
+        outs = [torch.empty(N, device="cuda") for _ in NAMES]
+        mats = [coot.Mat(t, 1, N, 1) if dim == 0 else coot.Mat(t, N, 1, N) for t in outs]
+        coot.coot_stats_dim(tree, dev, dim, 0x3F, mats, ws=ws)
+        torch.cuda.synchronize()
+        idx = np.unique(np.concatenate([[0, N - 1], rng.choice(N, 46, replace=False)]))
+        got = {name: outs[b].cpu().numpy()[idx].astype(np.float64) for b, name in enumerate(NAMES)}
+        every = np.arange(N)
+        sub = _sub(host, every, idx) if dim == 0 else _sub(host, idx, every)
+        check_stats(tree, sub, dim, got)
+
+
+def test_views_workload_8192():
+    """The views workload: the matrix tree over the 6144 x 6144 window at
+    (1024, 1024) of the 8192 x 8192 inputs (ld 8192), stored into the same
+    window of an output whose other elements must stay untouched, then the
+    column and row sums of the stored window, at the benchmark's launch
+    shapes; sampled lines and elements against the oracle."""
+    seed = synth.BASE_SEED + 1
+    host = [synth.as_mat(synth.uniform_f32(seed + k, N * N, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
+                         "f32", N, N) for k in range(4)]
+    full = [coot.Mat(torch.from_numpy(h.buf).cuda(), N, N, N) for h in host]
+    w0, w1 = N // 8, N - N // 8 - 1
+    n = w1 - w0 + 1
+    mats = [m.submat(w0, w0, w1, w1) for m in full]
+    out = torch.full((N * N,), float("nan"), device="cuda")
+    O1 = coot.Mat(out, N, N, N).submat(w0, w0, w1, w1)
+    col = torch.empty(n, device="cuda")
+    row = torch.empty(n, device="cuda")
+    ws = coot.Workspace(n)
+    t_expr = serialize(synth.MAT_EXPR)
+    leaf = serialize(synth.LEAF0)
+    coot.coot_expr_eval(t_expr, mats, O1)
+    coot.coot_sum_dim(leaf, [O1], 0, coot.Mat(col, 1, n, 1), ws=ws)
+    coot.coot_sum_dim(leaf, [O1], 1, coot.Mat(row, n, 1, n), ws=ws)
+    torch.cuda.synchronize()
+    o = out.view(N, N).T.cpu().numpy()  # (rows, cols)
+    assert np.isnan(o[:w0, :]).all() and np.isnan(o[w1 + 1:, :]).all()
+    assert np.isnan(o[:, :w0]).all() and np.isnan(o[:, w1 + 1:]).all()
+
+    rng = np.random.default_rng(3)
+    win = np.arange(w0, w1 + 1)
+    ri = np.unique(np.concatenate([[w0, w1], rng.choice(win, 62, replace=False)]))
+    ci = np.unique(np.concatenate([[w0, w1], rng.choice(win, 62, replace=False)]))
+    # sums of the stored window: the oracle's tree values, each with its
+    # error bound and the FP32 rounding of the store
+    vc, bc, unsafe = O.error_bound(t_expr, _sub(host, win, ci))
+    assert not unsafe.any()
+    gc = col.cpu().numpy()[ci - w0].astype(np.float64)
+    for k in range(len(ci)):
+        assert_sum_close(gc[k], O._fsum(vc[:, k]), vc[:, k], np.hypot(bc[:, k], vc[:, k] * 2.0 ** -24),
+                         f"column {ci[k]}")
+    vr, br, unsafe = O.error_bound(t_expr, _sub(host, ri, win))
+    assert not unsafe.any()
+    gr = row.cpu().numpy()[ri - w0].astype(np.float64)
+    for k in range(len(ri)):
+        assert_sum_close(gr[k], O._fsum(vr[k, :]), vr[k, :], np.hypot(br[k, :], vr[k, :] * 2.0 ** -24),
+                         f"row {ri[k]}")
+    got = np.ascontiguousarray(o[np.ix_(ri, ci)].ravel(order="F"))
+    check_elementwise(t_expr, _sub(host, ri, ci), synth.as_mat(got, "f32", len(ri), len(ci)))
+
+
+def test_convert_workload_8192():
+    """The conversion workload: B = 2 A + 1 with A an 8192 x 8192 int32
+    matrix (values in [-1e6, 1e6)) and B FP32, fused in one kernel and in
+    two steps (convert into an FP32 temporary, then evaluate).  Every result
+    is an integer below 2^24 in magnitude, so both paths must give 2 A + 1
+    exactly, element for element."""
+    u = synth.uniform01(synth.BASE_SEED + 5, N * N)
+    ha = np.floor(-1e6 + u * 2e6).astype(np.int32)
+    want = (2.0 * ha.astype(np.float64) + 1.0).astype(np.float32)
+    a = torch.from_numpy(ha).cuda()
+    tmp = torch.empty(N * N, device="cuda")
+    out = torch.empty(N * N, device="cuda")
+    A, T, B = (coot.Mat(t, N, N, N) for t in (a, tmp, out))
+    expr = serialize(("add", ("mul", synth.C(2.0), synth.X(0)), synth.C(1.0)))
+    coot.coot_expr_eval(expr, [A], B)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+    out.fill_(float("nan"))
+    coot.coot_expr_eval(serialize(synth.LEAF0), [A], T)
+    coot.coot_expr_eval(expr, [T], B)
+    torch.cuda.synchronize()
+    assert np.array_equal(tmp.cpu().numpy(), ha.astype(np.float32))
+    assert np.array_equal(out.cpu().numpy(), want)
