@@ -12,8 +12,9 @@ FP32 column-major 8192 x 8192 matrices A, B, C ~ U[-1, 1], D ~ U[0, 2]
 i.e. coot_expr_reduce (5 matrix streams), coot_expr_eval (5), and two
 coot_sum_dim over the stored out (1 each): 12 matrix streams of 268 MB =
 3.22 GB of algorithmic traffic per step.  `value` is that traffic over the
-device time of the step (GB/s); the inputs (1.07 GB) are larger than L2, so
-no flush is needed between steps.
+device time of the step (GB/s), the step captured once as a CUDA graph and
+replayed; the inputs (1.07 GB) are larger than L2, so no flush is needed
+between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl coot|reference]
 
@@ -300,19 +301,19 @@ def run_coot(args):
     ROW = coot.Mat(row, N, 1, N)
     names = list(STREAMS)
 
-    def step(ev=None):
+    def step(ev=None, s=None):
         if ev is not None:
             ev[0].record(stream)
-        coot.coot_expr_reduce(t_expr, mats, heads, out=O1, out_dev=res, ws=ws)
+        coot.coot_expr_reduce(t_expr, mats, heads, out=O1, out_dev=res, ws=ws, stream=s)
         if ev is not None:
             ev[1].record(stream)
-        coot.coot_expr_eval(t_chain, mats, O2, ws=ws)
+        coot.coot_expr_eval(t_chain, mats, O2, ws=ws, stream=s)
         if ev is not None:
             ev[2].record(stream)
-        coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws)
+        coot.coot_sum_dim(leaf, [O1], 0, COL, ws=ws, stream=s)
         if ev is not None:
             ev[3].record(stream)
-        coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws)
+        coot.coot_sum_dim(leaf, [O1], 1, ROW, ws=ws, stream=s)
         if ev is not None:
             ev[4].record(stream)
 
@@ -339,24 +340,36 @@ def run_coot(args):
     pci = None
     if hasattr(props, "pci_bus_id"):
         pci = f"{getattr(props, 'pci_domain_id', 0):08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    # The timed steps: the step's four calls captured once as a CUDA graph
+    # and replayed (their launches queue without host work in between), K
+    # replays between barriers.
+    g_step = _graph(torch, lambda s=None: step(None, s))
+    for _ in range(max(args.warmup, 3)):
+        g_step.replay()
     clocks = Clocks(local, pci)
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for k in range(args.steps):
-        step(evs[k])
+        g_step.replay()
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
+    ms_step = t_start.elapsed_time(t_end) / args.steps
+    # Per-call device times (calls, roofline): K more steps issued call by
+    # call with an event between calls, timed the same way.  The events
+    # cost the step about 2%, so they stay out of the steps above.
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        step(evs[k])
+    barrier()
     per_call = {n: [] for n in names}
     for k in range(args.steps):
         for i, n in enumerate(names):
             per_call[n].append(evs[k][i].elapsed_time(evs[k][i + 1]))
-    ms_step = ms_total / args.steps
     if world > 1:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -541,6 +554,8 @@ def run_coot(args):
             "config": {"workload": WORKLOAD if N == 8192 else WORKLOAD.replace("8192x8192", f"{N}x{N}"),
                        "n_rows": N, "n_cols": N, "step_bytes": STEP_BYTES,
                        "l2": f"inputs larger than L2 ({4 * MAT_BYTES / 1e9:.2f} GB of inputs per step), no flush",
+                       "timing": "the step's four calls captured once as a CUDA graph and replayed K times; "
+                                 "per-call times from K more steps issued call by call with events",
                        "parallelism": f"replicas x{world}"},
             "frac_of_hbm_peak": round(value / world / peak, 4),
             "unfused": None if ms_unfused is None else {
