@@ -633,15 +633,29 @@ def run_vectors(args):
         coot.coot_accu(t_schur, [X, Z], out_dev=res[0:1], ws=ws, stream=s)
         coot.coot_norm(leaf, [X], 2, out_dev=res[1:2], ws=ws, stream=s)
 
+    # the same three results from one coot_expr_multi call: x and z read once
+    trees = [t_axpy, t_schur, leaf]
+    heads = [0, coot.HEAD_SUM, coot.HEAD_NORM2]
+
+    def step_multi(s=None):
+        coot.coot_expr_multi(trees, [X, Z], [Y, None, None], heads, out_dev=res, ws=ws, stream=s)
+
     stream = torch.cuda.current_stream()
     ms = _timed(torch, stream, step, args.steps, args.warmup)
     g = _graph(torch, step)
     ms_g = _timed(torch, stream, g.replay, args.steps, args.warmup)
+    ms_m = _timed(torch, stream, step_multi, args.steps, args.warmup)
+    gm = _graph(torch, step_multi)
+    ms_mg = _timed(torch, stream, gm.replay, args.steps, args.warmup)
     nbytes = (3 + 2 + 1) * n * 4
     print(json.dumps({"metric": "fused vector step latency", "workload": "vectors n=1e6 fp32: 2x+3z, accu(x%z), "
                       "norm2(x)", "us_per_step": round(ms * 1e3, 2), "us_per_step_graph": round(ms_g * 1e3, 2),
                       "gbs_graph": round(nbytes / (ms_g * 1e-3) / 1e9, 1), "bytes_per_step": nbytes,
-                      "launches_per_step": 3, "note": "24 MB per step is L2-resident: latency, not HBM, bound"}))
+                      "launches_per_step": 3,
+                      "one_pass": {"us_per_step": round(ms_m * 1e3, 2), "us_per_step_graph": round(ms_mg * 1e3, 2),
+                                   "launches_per_step": 1, "bytes_per_step": 3 * n * 4,
+                                   "call": "coot_expr_multi: 2x+3z stored, accu(x%z), norm2(x)"},
+                      "note": "24 MB per step is L2-resident: latency, not HBM, bound"}))
 
 
 def run_precision(args, dt):

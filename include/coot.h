@@ -224,8 +224,8 @@ coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
 
 /* Launch shape of the kernels of one kind (0 element-wise / with heads,
  * 1 reductions only, 2 column sums, 3 row sums, 4 batched, 5 column
- * statistics, 6 row statistics; row statistics use at most 256 threads per
- * block) for the calls
+ * statistics, 6 row statistics, 7 several trees in one pass; row
+ * statistics use at most 256 threads per block) for the calls
  * that follow ON THIS THREAD, for tuning and for the learned selection of
  * launch shapes (not in the paper).  block: threads per block, 64..1024 in
  * steps of 64, or 0 to drop the setting (back to the built-in choice);
@@ -290,8 +290,9 @@ coot_status coot_tree_compile(const uint8_t* tree, size_t tree_len, int kind, in
 /* Write the CUDA source generated for a tree into buf (NUL-terminated,
  * truncated to buf_len) and its full length to *len.  kind: 0 = element-wise
  * evaluation, 1 = full reduction, 2 = column sums, 3 = row sums,
- * 4 = batched evaluation, 5 / 6 = column / row statistics (all six); every
- * input and the output FP32.  Host-only;
+ * 4 = batched evaluation, 5 / 6 = column / row statistics (all six),
+ * 7 = the several-tree kernel with this one tree; every input and the
+ * output FP32.  Host-only;
  * for inspection and tests. */
 coot_status coot_tree_source(const uint8_t* tree, size_t tree_len, int kind, char* buf,
                              size_t buf_len, size_t* len);
@@ -356,6 +357,31 @@ coot_status coot_minmax(const uint8_t* tree, size_t tree_len, const coot_mat* in
 coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_mat* in, int n_in,
                              unsigned heads, const coot_mat* out, double* out_dev, void* ws,
                              size_t ws_bytes, void* stream);
+
+/* Several trees over the same operands in ONE pass (the delayed evaluation
+ * of Section 7 extended to several expressions of one assignment group):
+ * every input element is read once for all trees.
+ *   trees[k], tree_lens[k]  host buffers, the serialised trees
+ *                           (k < n_trees, 1 <= n_trees <= 4); each tree
+ *                           reads the first tree_inputs(k) <= n_in operands
+ *                           and all trees share tree 0's compute type;
+ *   in[0 .. n_in)           the operands (equal shapes, 1 <= n_in <= 4);
+ *   outs                    NULL, or n_trees matrices: tree k is stored
+ *                           into outs[k] when outs[k].ptr is not NULL
+ *                           (same shape; it may be identical to an input,
+ *                           every element's inputs being read before any
+ *                           value is stored, and must not overlap another
+ *                           stored tree: COOT_ERR_ALIAS);
+ *   heads                   NULL, or n_trees masks of COOT_HEAD_* bits;
+ *   out_dev                 device FP64 results: tree 0's heads in
+ *                           increasing bit order, then tree 1's, ...
+ * A tree with neither an output nor heads is an argument error.  Results,
+ * summation order and the empty and NaN rules are those of coot_expr_reduce
+ * for each tree; the workspace needs room for the partials of every head
+ * of every tree. */
+coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens, int n_trees,
+                            const coot_mat* in, int n_in, const coot_mat* outs, const unsigned* heads,
+                            double* out_dev, void* ws, size_t ws_bytes, void* stream);
 
 /* Submatrix views (Table 1: .rows(a, b), .cols(c, d), .submat(p, q, r, s),
  * .row(i), .col(j)): the view of rows r0..r1 and columns c0..c1, inclusive,

@@ -24,7 +24,7 @@ from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_I32, COOT_NORM_
                    COOT_U32,
                    HEAD_ALL, HEAD_ANY, HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM,
                    HEAD_SUMABS, HEAD_SUMSQ, KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE,
-                   KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
+                   KIND_MULTI, KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
                    CootError, coot_mat)
 from .expr import (Expr, abs_, acos, asin, atan, const, cos, eq, exp, log, log10, ne, pow_, serialize, sin, sqrt,
                    square, tan, var)
@@ -32,7 +32,7 @@ from .expr import (Expr, abs_, acos, asin, atan, const, cos, eq, exp, log, log10
 __all__ = [
     "Mat", "Workspace", "CootError", "coot_init", "coot_finalize", "coot_workspace_size", "coot_tree_check",
     "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
-    "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_unfused_eval",
+    "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_expr_multi", "coot_unfused_eval",
     "coot_unfused_tmp_count", "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "eq", "ne",
     "pow_", "log10", "sin", "cos", "tan", "asin", "acos", "atan", "serialize",
     "batch_item", "coot_batch_plan", "coot_expr_eval_batched",
@@ -224,6 +224,29 @@ def coot_expr_reduce(tree: bytes, ins, heads: int, out: Mat | None = None, out_d
     o = ctypes.byref(out.c()) if out is not None else None
     _abi.call("coot_expr_reduce", tree, len(tree), arr, n, heads, o, ctypes.c_void_p(res.data_ptr()), w.ptr,
               w.bytes, _stream(stream))
+    return res
+
+
+def coot_expr_multi(trees, ins, outs=None, heads=None, out_dev=None, ws=None, stream=None):
+    """Several trees over the same operands in one pass: tree k is stored
+    into outs[k] (a Mat, or None) and reduced by heads[k] (a HEAD_* mask, or
+    0).  Returns the FP64 device tensor of results (tree 0's heads in
+    increasing bit order, then tree 1's, ...), or None without heads."""
+    nt = len(trees)
+    keep = [ctypes.create_string_buffer(bytes(t), len(t)) for t in trees]
+    tp = (ctypes.c_void_p * nt)(*[ctypes.cast(b, ctypes.c_void_p) for b in keep])
+    tl = (ctypes.c_size_t * nt)(*[len(t) for t in trees])
+    arr, n = _mats(ins)
+    o_arr = None
+    if outs is not None:
+        o_arr = (coot_mat * nt)(*[m.c() if m is not None else coot_mat() for m in outs])
+    hs = list(heads) if heads is not None else [0] * nt
+    h_arr = (ctypes.c_uint * nt)(*hs)
+    total = sum(bin(h).count("1") for h in hs)
+    res = _result(out_dev, total) if total else None
+    w = _ws(ws, 0)
+    _abi.call("coot_expr_multi", tp, tl, nt, arr, n, o_arr, h_arr,
+              ctypes.c_void_p(res.data_ptr()) if res is not None else None, w.ptr, w.bytes, _stream(stream))
     return res
 
 

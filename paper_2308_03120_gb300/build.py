@@ -40,7 +40,8 @@ def cuda_home() -> str:
     raise RuntimeError("CUDA toolkit not found (set CUDA_HOME)")
 
 
-JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh", "jit_stats.cuh"]
+JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh", "jit_stats.cuh",
+               "jit_multi.cuh"]
 
 
 def _embed_runtime() -> str:

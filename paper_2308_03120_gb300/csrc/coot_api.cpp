@@ -156,14 +156,15 @@ static coot_status check_alias(const coot_mat& out, const coot_mat* in, int n_in
 // n_cols, per-operand ld).  When every operand is dense (ld == n_rows or a
 // single column) the whole object is one long column.
 struct View {
-  const void* ptr[5];
-  int64_t ld[5];
-  int dtype[5];
-  int n = 0;  // operands (inputs, then the stored output if any)
+  const void* ptr[8];
+  int64_t ld[8];
+  int dtype[8];
+  int n = 0;  // operands (inputs, then the stored outputs if any)
   int64_t n_rows = 0, n_cols = 0;
 };
 
-static View make_view(const coot_mat* in, int n_in, const coot_mat* out) {
+static View make_view(const coot_mat* in, int n_in, const coot_mat* out, const coot_mat* const* more_outs = nullptr,
+                      int n_more = 0) {
   View v;
   v.n_rows = in[0].n_rows;
   v.n_cols = in[0].n_cols;
@@ -177,6 +178,12 @@ static View make_view(const coot_mat* in, int n_in, const coot_mat* out) {
     v.ptr[v.n] = out->ptr;
     v.ld[v.n] = out->ld;
     v.dtype[v.n] = out->dtype;
+    ++v.n;
+  }
+  for (int i = 0; i < n_more; ++i) {
+    v.ptr[v.n] = more_outs[i]->ptr;
+    v.ld[v.n] = more_outs[i]->ld;
+    v.dtype[v.n] = more_outs[i]->dtype;
     ++v.n;
   }
   bool dense = true;
@@ -218,7 +225,7 @@ struct Launch {
 // A launch shape set by the caller for the calls that follow on this
 // thread (tuning, learned selection); block == 0 means "not set".
 static thread_local Launch g_override[KIND_COUNT] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0},
-                                                     {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
+                                                     {1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
 // The shape of the last launch on this thread.
 static thread_local Launch g_last;
 static thread_local int64_t g_last_grid = 0;
@@ -700,7 +707,7 @@ int coot_version(void) { return 100; }
 
 coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm, int64_t split) {
   clear_error();
-  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..6");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..7");
   if (block == 0) {
     g_override[kind] = Launch{1, 1, 0};
     return COOT_OK;
@@ -815,13 +822,21 @@ coot_status coot_tree_check(const uint8_t* tree, size_t len, int* n_inputs, int*
 }
 
 static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype, unsigned heads, KernelSpec* spec) {
-  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..6");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..7");
   if (dtype_size(in_dtype) == 0 || dtype_size(out_dtype) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
   spec->kind = kind;
   for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
   spec->out_dtype = out_dtype;
   spec->store = kind == KIND_MAP || kind == KIND_BATCHED;
   spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
+  if (kind == KIND_MULTI) {
+    // one tree, stored and reduced by `heads`
+    spec->store = false;
+    spec->n_trees = 1;
+    spec->trees = &t;
+    spec->tree_heads[0] = heads;
+    spec->tree_out[0] = out_dtype;
+  }
   spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
   spec->unroll = 2;
   spec->block = 256;
@@ -879,6 +894,126 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t len, const coot_mat* in
   if (heads & ~COOT_HEAD_MASK) return fail(COOT_ERR_INVALID_ARG, "unknown head bits");
   if (heads == 0 && out == nullptr) return fail(COOT_ERR_INVALID_ARG, "nothing to compute");
   return run_map_reduce(o.t, o.in, o.n, heads, out, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens, int n_trees, const coot_mat* in,
+                            int n_in, const coot_mat* outs, const unsigned* heads, double* out_dev, void* ws,
+                            size_t ws_bytes, void* stream) {
+  clear_error();
+  if (trees == nullptr || tree_lens == nullptr || n_trees < 1 || n_trees > 4)
+    return fail(COOT_ERR_INVALID_ARG, "1 to 4 trees");
+  if (in == nullptr || n_in < 1 || n_in > COOT_TREE_MAX_INPUTS) return fail(COOT_ERR_INVALID_ARG, "1 to 4 inputs");
+  for (int i = 0; i < n_in; ++i) {
+    coot_status s = check_mat(&in[i], "input");
+    if (s != COOT_OK) return s;
+    if (in[i].n_rows != in[0].n_rows || in[i].n_cols != in[0].n_cols)
+      return fail(COOT_ERR_SHAPE, "element-wise operands need equal sizes: input " + std::to_string(i));
+  }
+  Tree ts[4];
+  const coot_mat* stored[4];
+  int n_stored = 0;
+  KernelSpec spec;
+  spec.kind = KIND_MULTI;
+  spec.n_trees = n_trees;
+  spec.trees = ts;
+  unsigned all_heads = 0;
+  int total_heads = 0;
+  for (int k = 0; k < n_trees; ++k) {
+    const std::string at = "tree " + std::to_string(k) + ": ";
+    coot_status s = parse_tree(trees[k], tree_lens[k], &ts[k]);
+    if (s != COOT_OK) return fail(s, at + coot_last_error());
+    canonical_in_place(&ts[k]);
+    if (ts[k].n_inputs > n_in) return fail(COOT_ERR_INVALID_ARG, at + "uses more inputs than given");
+    if (ts[k].compute != ts[0].compute) return fail(COOT_ERR_DTYPE, at + "compute type differs from tree 0's");
+    const unsigned h = heads ? heads[k] : 0u;
+    if (h & ~COOT_HEAD_MASK) return fail(COOT_ERR_INVALID_ARG, at + "unknown head bits");
+    spec.tree_heads[k] = h;
+    all_heads |= h;
+    total_heads += popcount(h);
+    if (outs != nullptr && outs[k].ptr != nullptr) {
+      s = check_mat(&outs[k], "output");
+      if (s != COOT_OK) return fail(s, at + coot_last_error());
+      if (outs[k].n_rows != in[0].n_rows || outs[k].n_cols != in[0].n_cols)
+        return fail(COOT_ERR_SHAPE, at + "output shape differs from the operands'");
+      spec.tree_out[k] = outs[k].dtype;
+      stored[n_stored++] = &outs[k];
+    } else if (h == 0) {
+      return fail(COOT_ERR_INVALID_ARG, at + "nothing to compute (no output, no heads)");
+    }
+  }
+  // outputs: each may be identical to an input (every element's inputs are
+  // read before any tree's value is stored), none may overlap another
+  bool aliased = false;
+  for (int a = 0; a < n_stored; ++a) {
+    bool al = false;
+    coot_status s = check_alias(*stored[a], in, n_in, true, &al);
+    if (s != COOT_OK) return s;
+    aliased = aliased || al;
+    for (int b = 0; b < a; ++b)
+      if (overlaps(*stored[a], *stored[b])) return fail(COOT_ERR_ALIAS, "two stored trees overlap");
+  }
+  const int64_t n = n_elem(in[0]);
+  if (total_heads > 0) {
+    if (out_dev == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
+    if (n == 0) {
+      if (all_heads & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
+      // sums and norms of nothing are 0, any() is 0, all() is 1
+      cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * total_heads, (cudaStream_t)stream);
+      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+      int base = 0;
+      for (int k = 0; k < n_trees; ++k) {
+        if (spec.tree_heads[k] & COOT_HEAD_ALL) {
+          const double* one = nullptr;
+          coot_status s = device_one(&one);
+          if (s != COOT_OK) return s;
+          e = cudaMemcpyAsync(out_dev + base + popcount(spec.tree_heads[k] & (COOT_HEAD_ALL - 1)), one, sizeof(double),
+                              cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+          if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+        }
+        base += popcount(spec.tree_heads[k]);
+      }
+      return COOT_OK;
+    }
+    if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * total_heads)
+      return fail(COOT_ERR_WORKSPACE, "reductions need a workspace (coot_workspace_size)");
+  } else if (n == 0) {
+    return COOT_OK;
+  }
+  // one launch: the synthetic tree carries the inputs and the compute type
+  Tree t;
+  t.n_inputs = n_in;
+  t.compute = ts[0].compute;
+  t.hash = 0;
+  const View v = make_view(in, n_in, nullptr, stored, n_stored);
+  CallInfo ci = call_info(KIND_MULTI, ts[0], in, n_in, n_stored ? stored[0]->dtype : -1, all_heads, v);
+  const Launch l = heuristic(KIND_MULTI, n_in, v, &ci);
+  for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
+  spec.vec = l.vec;
+  spec.unroll = l.unroll;
+  spec.block = l.block;
+  spec.nc = !aliased;
+  const Compiled* c = nullptr;
+  coot_status s = kernel_for(t, spec, &c);
+  if (s != COOT_OK) return s;
+  coot_multi_params_host mp;
+  std::memset(&mp, 0, sizeof mp);
+  fill_io(&mp.b, v, n_in);
+  for (int k = 0, j = 0; k < n_trees; ++k) {
+    if (spec.tree_out[k] < 0) continue;
+    mp.out[k] = const_cast<void*>(v.ptr[n_in + j]);
+    mp.ld_out[k] = v.ld[n_in + j];
+    ++j;
+  }
+  mp.b.ws = (unsigned char*)ws;
+  mp.b.res = out_dev;
+  const int64_t tile = tile_rows(l);
+  const int64_t units = ((v.n_rows + tile - 1) / tile) * v.n_cols;
+  int64_t max_grid = INT32_MAX;
+  if (total_heads > 0) {
+    const int64_t fit = (int64_t)((ws_bytes - COOT_WS_PARTIALS_OFF) / (sizeof(double) * total_heads));
+    max_grid = std::min<int64_t>(COOT_MAX_GRID, fit);
+  }
+  return launch(c, units, max_grid, l, &mp.b, stream, &mp);
 }
 
 coot_status coot_accu(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,

@@ -44,7 +44,8 @@ enum Kind {
   KIND_BATCHED = 4,
   KIND_COLSTATS = 5,
   KIND_ROWSTATS = 6,
-  KIND_COUNT = 7
+  KIND_MULTI = 7,
+  KIND_COUNT = 8
 };
 
 // Everything that selects one compiled kernel.
@@ -58,6 +59,13 @@ struct KernelSpec {
   int unroll = 1;
   int block = 256;
   bool nc = true;  // inputs read through the non-coherent path
+  // several trees in one pass (KIND_MULTI): the trees (n_trees of them, all
+  // over the same inputs), each one's reduction heads and its output
+  // storage code (-1 when it is not stored)
+  int n_trees = 0;
+  const Tree* trees = nullptr;
+  unsigned tree_heads[4] = {0, 0, 0, 0};
+  int tree_out[4] = {-1, -1, -1, -1};
 };
 
 // Full CUDA source of one kernel: the prelude, the tree function and the
@@ -165,6 +173,14 @@ struct coot_stats_params_host {
   int64_t norm_type;
 };
 static_assert(sizeof(coot_stats_params_host) == 8 * 31, "coot_stats_params layout");
+
+// Launch parameters of the several-tree kernel (coot_multi_params in
+// jit_multi.cuh).
+struct coot_multi_params_host {
+  coot_params_host b;
+  void* out[4];
+  int64_t ld_out[4];
+};
 
 // Workspace layout (offsets in bytes), mirrored in jit_rt.cuh.
 #define COOT_WS_COUNTER_OFF 128

@@ -7,6 +7,7 @@
 // node's apply() launching at least one kernel (Section 7); here the whole
 // tree becomes one straight-line device function that the kernels of
 // jit_rt.cuh call once per element.
+#include <algorithm>
 #include <cinttypes>
 #include <cmath>
 #include <cstdio>
@@ -111,13 +112,13 @@ static std::string literal(double v, int compute) {
   return b;
 }
 
-static std::string tree_function(const Tree& t) {
+static std::string tree_function(const Tree& t, const char* name = "coot_f") {
   const bool f32 = t.compute == COOT_F32;
   const char* fexp = f32 ? "expf" : "exp";
   const char* flog = f32 ? "logf" : "log";
   const char* fsqrt = f32 ? "sqrtf" : "sqrt";
   const char* fabs_ = f32 ? "fabsf" : "fabs";
-  std::string s = "__device__ __forceinline__ COOT_REAL coot_f(const COOT_REAL* x) {\n";
+  std::string s = std::string("__device__ __forceinline__ COOT_REAL ") + name + "(const COOT_REAL* x) {\n";
   for (size_t k = 0; k < t.nodes.size(); ++k) {
     const Node& n = t.nodes[k];
     const std::string a = "t" + std::to_string(n.a), b = "t" + std::to_string(n.b);
@@ -165,6 +166,7 @@ const char* entry_name(const KernelSpec& spec) {
     case KIND_ROWSUM: return "coot_rowsum";
     case KIND_COLSTATS: return "coot_colstats";
     case KIND_ROWSTATS: return "coot_rowstats";
+    case KIND_MULTI: return "coot_multi";
     default: return "coot_batched";
   }
 }
@@ -185,7 +187,33 @@ std::string generate_source(const Tree& t, const KernelSpec& spec) {
                 spec.block,
                 spec.nc ? 1 : 0);
   std::string src(pre);
-  src += tree_function(t);
+  if (spec.kind == KIND_MULTI) {
+    // several trees over the same inputs: coot_ft0 .. coot_ft3 (slots past
+    // n_trees hold a constant that no code path reads), each tree's heads,
+    // whether it is stored and its storage code
+    const int nt = spec.n_trees;
+    char m[512];
+    std::snprintf(m, sizeof m,
+                  "#define COOT_NT %d\n"
+                  "#define COOT_HEADS_0 %uu\n#define COOT_HEADS_1 %uu\n#define COOT_HEADS_2 %uu\n#define COOT_HEADS_3 %uu\n"
+                  "#define COOT_STORE_0 %d\n#define COOT_STORE_1 %d\n#define COOT_STORE_2 %d\n#define COOT_STORE_3 %d\n"
+                  "#define COOT_TO_0 %d\n#define COOT_TO_1 %d\n#define COOT_TO_2 %d\n#define COOT_TO_3 %d\n",
+                  nt, spec.tree_heads[0], spec.tree_heads[1], spec.tree_heads[2], spec.tree_heads[3],
+                  spec.tree_out[0] >= 0, spec.tree_out[1] >= 0, spec.tree_out[2] >= 0, spec.tree_out[3] >= 0,
+                  std::max(spec.tree_out[0], 0), std::max(spec.tree_out[1], 0), std::max(spec.tree_out[2], 0),
+                  std::max(spec.tree_out[3], 0));
+    src += m;
+    for (int k = 0; k < 4; ++k) {
+      const std::string name = "coot_ft" + std::to_string(k);
+      if (k < nt && spec.trees) {
+        src += tree_function(spec.trees[k], name.c_str());
+      } else {
+        src += "__device__ __forceinline__ COOT_REAL " + name + "(const COOT_REAL* x) { return (COOT_REAL)0; }\n";
+      }
+    }
+  } else {
+    src += tree_function(t);
+  }
   src += coot_jit_rt_source;
   return src;
 }

@@ -556,7 +556,10 @@ __device__ __forceinline__ float coot_pairwise2(const float* y, int what) {
 // all / any: 1 for a nonzero value (NaN included), else 0
 __device__ __forceinline__ COOT_REAL coot_nonzero(COOT_REAL y) { return y != (COOT_REAL)0 ? (COOT_REAL)1 : (COOT_REAL)0; }
 
-struct coot_acc {
+// Per-thread accumulators of the reduction heads in the mask H
+// (COOT_HEAD_* bits).
+template <unsigned H>
+struct coot_acc_h {
   COOT_REAL s, sc;   // sum
   COOT_REAL q, qc;   // sum of squares
   COOT_REAL a, ac;   // sum of magnitudes
@@ -577,15 +580,15 @@ struct coot_acc {
     mxa = (COOT_REAL)0;
   }
   __device__ __forceinline__ void add(COOT_REAL y) {
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, y);
-    if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_sq(y));
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_abs(y));
-    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y);
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y);
-    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
-    if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y));
-    if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y));
+    if constexpr ((H & COOT_HEAD_SUM) != 0) coot_two_sum(s, sc, y);
+    if constexpr ((H & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_sq(y));
+    if constexpr ((H & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_abs(y));
+    if constexpr ((H & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y);
+    if constexpr ((H & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y);
+    if constexpr ((H & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y));
+    if constexpr ((H & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y));
+    if constexpr ((H & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y));
+    if constexpr ((H & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y));
   }
   // V consecutive values.  The plain sum adds every value with TwoSum (no
   // rounding is lost however the terms cancel).  Sums of squares and of
@@ -602,26 +605,26 @@ struct coot_acc {
 #endif
     if constexpr (packed) {
 #if !COOT_REAL_F64
-      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) {
+      if constexpr ((H & COOT_HEAD_SUM) != 0) {
 #pragma unroll
         for (int v = 0; v < V / 2; ++v) coot_two_sum2(s2, sc2, coot_pack(y[2 * v], y[2 * v + 1]));
       }
-      if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
-      if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
+      if constexpr ((H & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
+      if constexpr ((H & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
 #endif
     } else {
-      if constexpr ((COOT_HEADS & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
-      if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
+      if constexpr ((H & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
+      if constexpr ((H & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0 && !packed) coot_two_sum(s, sc, y[v]);
-      if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
-      if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
-      if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
-      if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y[v]));
-      if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y[v]));
-      if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y[v]));
+      if constexpr ((H & COOT_HEAD_SUM) != 0 && !packed) coot_two_sum(s, sc, y[v]);
+      if constexpr ((H & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
+      if constexpr ((H & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
+      if constexpr ((H & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
+      if constexpr ((H & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y[v]));
+      if constexpr ((H & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y[v]));
+      if constexpr ((H & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y[v]));
     }
   }
   // per-head values as FP64, in head-bit order
@@ -629,7 +632,7 @@ struct coot_acc {
   // normalised; extrema as (value, 0))
   __device__ __forceinline__ void values(COOT_REAL* h, COOT_REAL* l) const {
     int k = 0;
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUM) != 0) {
+    if constexpr ((H & COOT_HEAD_SUM) != 0) {
       coot_dw_norm(s, sc, h[k], l[k]);
 #if !COOT_REAL_F64
       // the two packed lanes, each an exact (sum, compensation) pair
@@ -644,25 +647,29 @@ struct coot_acc {
 #endif
       ++k;
     }
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMSQ) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_NORM2) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_SUMABS) != 0) { coot_dw_norm(a, ac, h[k], l[k]); ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_MIN) != 0) { h[k] = mn; l[k] = 0; ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAX) != 0) { h[k] = mx; l[k] = 0; ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_MINABS) != 0) { h[k] = mna; l[k] = 0; ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_MAXABS) != 0) { h[k] = mxa; l[k] = 0; ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_ALL) != 0) { h[k] = alz; l[k] = 0; ++k; }
-    if constexpr ((COOT_HEADS & COOT_HEAD_ANY) != 0) { h[k] = anz; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_SUMSQ) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
+    if constexpr ((H & COOT_HEAD_NORM2) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
+    if constexpr ((H & COOT_HEAD_SUMABS) != 0) { coot_dw_norm(a, ac, h[k], l[k]); ++k; }
+    if constexpr ((H & COOT_HEAD_MIN) != 0) { h[k] = mn; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_MAX) != 0) { h[k] = mx; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_MINABS) != 0) { h[k] = mna; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_MAXABS) != 0) { h[k] = mxa; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_ALL) != 0) { h[k] = alz; l[k] = 0; ++k; }
+    if constexpr ((H & COOT_HEAD_ANY) != 0) { h[k] = anz; l[k] = 0; ++k; }
     (void)k;
   }
 };
+typedef coot_acc_h<COOT_HEADS> coot_acc;
 
-// combine rule of head number k (in bit order among the set bits)
-__device__ __forceinline__ unsigned coot_head_bit(int k) {
-  unsigned m = COOT_HEADS;
+// combine rule of head number k of the mask H (in bit order among the set
+// bits)
+template <unsigned H>
+__device__ __forceinline__ unsigned coot_head_bit_of(int k) {
+  unsigned m = H;
   for (int i = 0; i < k; ++i) m &= m - 1;
   return m & (~m + 1);
 }
+__device__ __forceinline__ unsigned coot_head_bit(int k) { return coot_head_bit_of<COOT_HEADS>(k); }
 
 // heads combined by a minimum / a maximum (the rest are sums)
 __device__ __forceinline__ bool coot_min_head(unsigned bit) {
@@ -684,7 +691,7 @@ __device__ __forceinline__ double coot_identity(unsigned bit) {
   return 0.0;
 }
 
-#if COOT_NHEADS > 0
+#if COOT_NHEADS > 0 || COOT_KIND == 7
 __device__ __forceinline__ COOT_REAL coot_identity_r(unsigned bit) {
   if (coot_min_head(bit)) return (COOT_REAL)COOT_INF_F;
   if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_ANY) return -(COOT_REAL)COOT_INF_F;
@@ -702,20 +709,20 @@ __device__ __forceinline__ void coot_combine_dw(unsigned bit, COOT_REAL& h, COOT
   }
 }
 
-// Block-level combine of every head in double-word arithmetic, one FP64
+// Block-level combine of NH heads in double-word arithmetic (head k,
+// this thread's value (h[k], l[k]), combined by the rule bit(k)), one FP64
 // partial per block and head, and the last-arriving block's ordered FP64
-// combine of the partials into p.res.
-__device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
-  __shared__ COOT_REAL red_h[COOT_NHEADS][COOT_WARPS];
-  __shared__ COOT_REAL red_l[COOT_NHEADS][COOT_WARPS];
+// combine of the partials into p.res[0 .. NH).
+template <int NH, typename Bit>
+__device__ void coot_finish_heads(COOT_REAL (&h)[NH], COOT_REAL (&l)[NH], Bit bit_of, const coot_params& p) {
+  __shared__ COOT_REAL red_h[NH][COOT_WARPS];
+  __shared__ COOT_REAL red_l[NH][COOT_WARPS];
   __shared__ double red64[COOT_WARPS];
   __shared__ int is_last;
-  COOT_REAL h[COOT_NHEADS], l[COOT_NHEADS];
-  acc.values(h, l);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < COOT_NHEADS; ++k) {
-    const unsigned bit = coot_head_bit(k);
+  for (int k = 0; k < NH; ++k) {
+    const unsigned bit = bit_of(k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const COOT_REAL yh = __shfl_down_sync(0xffffffffu, h[k], o);
@@ -731,8 +738,8 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
   double* part = (double*)(p.ws + COOT_WS_PARTIALS_OFF);
   if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < COOT_NHEADS; ++k) {
-      const unsigned bit = coot_head_bit(k);
+    for (int k = 0; k < NH; ++k) {
+      const unsigned bit = bit_of(k);
       COOT_REAL wh = lane < COOT_WARPS ? red_h[k][lane] : coot_identity_r(bit);
       COOT_REAL wl = lane < COOT_WARPS ? red_l[k][lane] : (COOT_REAL)0;
 #pragma unroll
@@ -754,8 +761,8 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
   __threadfence();
   // the last block: every thread folds a strided subset of the partials in
   // index order (FP64), then the block combines the thread results
-  for (int k = 0; k < COOT_NHEADS; ++k) {
-    const unsigned bit = coot_head_bit(k);
+  for (int k = 0; k < NH; ++k) {
+    const unsigned bit = bit_of(k);
     double w = coot_identity(bit);
     for (coot_u32 b = threadIdx.x; b < gridDim.x; b += COOT_BLOCK)
       w = coot_combine(bit, w, __ldcg(part + (coot_i64)k * gridDim.x + b));
@@ -777,4 +784,14 @@ __device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
   }
   if (threadIdx.x == 0) *(coot_u32*)(p.ws + COOT_WS_COUNTER_OFF) = 0u;
 }
+
+#if COOT_NHEADS > 0
+// every head of the kernel's mask COOT_HEADS
+__device__ void coot_finish_full(const coot_acc& acc, const coot_params& p) {
+  COOT_REAL h[COOT_NHEADS], l[COOT_NHEADS];
+  acc.values(h, l);
+  coot_finish_heads<COOT_NHEADS>(h, l, [](int k) { return coot_head_bit(k); }, p);
+}
+#endif
+
 #endif

@@ -204,6 +204,51 @@ def test_reduction_argument_errors():
     assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "head" in msg
 
 
+def test_multi_tree_argument_errors():
+    """coot_expr_multi (several trees in one pass) rejects bad calls before
+    any device work."""
+    t1, t2 = serialize(synth.AXPY_2X_3Z), serialize(synth.SCHUR_XZ)
+    ins = (_abi.coot_mat * 2)(_fake(10, 3), _fake(10, 3, ptr=1 << 24))
+    res = ctypes.c_void_p(1 << 30)
+    ws = ctypes.c_void_p(1 << 32)
+
+    def call(trees, n_in=2, outs=None, heads=None, w=ws, wb=1 << 22, nt=None):
+        keep = [ctypes.create_string_buffer(bytes(t), len(t)) for t in trees]
+        tp = (ctypes.c_void_p * max(len(trees), 1))(*[ctypes.cast(b, ctypes.c_void_p) for b in keep])
+        tl = (ctypes.c_size_t * max(len(trees), 1))(*[len(t) for t in trees])
+        o = (_abi.coot_mat * len(outs))(*outs) if outs is not None else None
+        h = (ctypes.c_uint * len(heads))(*heads) if heads is not None else None
+        return _call("coot_expr_multi", tp, tl, len(trees) if nt is None else nt, ins, n_in, o, h, res, w, wb, None)
+
+    st, _ = call([t1], nt=0)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    st, _ = call([t1] * 5)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
+    # a tree with neither an output nor heads
+    st, msg = call([t1, t2], heads=[1, 0])
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "tree 1" in msg
+    # a tree reading more operands than given
+    st, msg = call([t1], n_in=1, heads=[1])
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "inputs" in msg
+    # compute types differ
+    st, _ = call([t1, serialize(synth.SCHUR_XZ, compute="f64")], heads=[1, 1])
+    assert _abi.STATUS[st] == "COOT_ERR_DTYPE"
+    st, msg = call([t1, t2], heads=[1, 1 << 10])
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "head" in msg
+    # two stored trees on the same memory; an output of another shape
+    o = _fake(10, 3, ptr=1 << 28)
+    st, _ = call([t1, t2], outs=[o, o])
+    assert _abi.STATUS[st] == "COOT_ERR_ALIAS"
+    st, _ = call([t1], outs=[_fake(10, 4, ptr=1 << 28)])
+    assert _abi.STATUS[st] == "COOT_ERR_SHAPE"
+    # an output overlapping an input without being identical to it
+    st, _ = call([t1], outs=[_fake(10, 3, ptr=(1 << 20) + 4)])
+    assert _abi.STATUS[st] == "COOT_ERR_ALIAS"
+    # heads need a workspace
+    st, _ = call([t1, t2], heads=[1, 4], w=None, wb=0)
+    assert _abi.STATUS[st] == "COOT_ERR_WORKSPACE"
+
+
 def test_stats_argument_errors():
     leaf = serialize(synth.LEAF0)
     m = (_abi.coot_mat * 1)(_fake(30, 40))
