@@ -244,8 +244,10 @@ coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int
  * would use with exactly this launch shape (vec 1/2/4/8, unroll 1..16):
  * first-use compilation moves out of timed regions and graph captures.
  * dtypes: host array of the tree's input storage types; out_dtype: -1 when
- * nothing element-wise is stored.  Thread-safe; threads compile in
- * parallel.  Needs coot_init. */
+ * nothing element-wise is stored.  Kinds 0..6; the several-tree kernel
+ * (kind 7) is compiled by its first coot_expr_multi call
+ * (COOT_ERR_UNSUPPORTED).  Thread-safe; threads compile in parallel.
+ * Needs coot_init. */
 coot_status coot_prepare(const uint8_t* tree, size_t tree_len, int kind, const int32_t* dtypes,
                          int out_dtype, unsigned heads, int block, int vec, int unroll);
 

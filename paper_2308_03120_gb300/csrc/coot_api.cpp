@@ -744,6 +744,8 @@ coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_
   if (s != COOT_OK) return s;
   canonical_in_place(&t);
   if (kind < 0 || kind >= KIND_COUNT || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
+  if (kind == KIND_MULTI)
+    return fail(COOT_ERR_UNSUPPORTED, "the several-tree kernel is compiled by its first coot_expr_multi call");
   if (block < 64 || block > 1024 || block % 64) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
   if (!(vec == 1 || vec == 2 || vec == 4 || vec == 8) || unroll < 1 || unroll > 16)
     return fail(COOT_ERR_INVALID_ARG, "vec must be 1, 2, 4 or 8 and unroll 1..16");
