@@ -380,27 +380,41 @@ static int popcount(unsigned m) {
 static int tile_rows(const Launch& l) { return l.block * l.vec * l.unroll; }
 
 // Element-wise evaluation and/or full reductions of one tree.
+// The heads of reductions over an empty object, for `n` groups of heads
+// (masks[k], results one group after another in increasing bit order):
+// sums, norms and any() are 0, all() is 1; min / max are an error.
+static coot_status empty_heads(double* res, const unsigned* masks, int n, void* stream) {
+  unsigned any_mask = 0;
+  int total = 0;
+  for (int k = 0; k < n; ++k) {
+    any_mask |= masks[k];
+    total += popcount(masks[k]);
+  }
+  if (any_mask & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
+  cudaError_t e = cudaMemsetAsync(res, 0, sizeof(double) * total, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  int base = 0;
+  for (int k = 0; k < n; ++k) {
+    if (masks[k] & COOT_HEAD_ALL) {
+      const double* one = nullptr;
+      coot_status s = device_one(&one);
+      if (s != COOT_OK) return s;
+      e = cudaMemcpyAsync(res + base + popcount(masks[k] & (COOT_HEAD_ALL - 1)), one, sizeof(double),
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    base += popcount(masks[k]);
+  }
+  return COOT_OK;
+}
+
 static coot_status run_map_reduce(const Tree& t, const coot_mat* in, int n_in, unsigned heads, const coot_mat* out,
                                   double* res, void* ws, size_t ws_bytes, void* stream) {
   const bool store = out != nullptr;
   const int64_t n = n_elem(in[0]);
   if (heads) {
     if (res == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
-    if (n == 0) {
-      if (heads & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
-      // sums and norms of nothing are 0, any() is 0, all() is 1
-      cudaError_t e = cudaMemsetAsync(res, 0, sizeof(double) * popcount(heads), (cudaStream_t)stream);
-      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-      if (heads & COOT_HEAD_ALL) {
-        const double* one = nullptr;
-        coot_status s = device_one(&one);
-        if (s != COOT_OK) return s;
-        e = cudaMemcpyAsync(res + popcount(heads & (COOT_HEAD_ALL - 1)), one, sizeof(double),
-                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
-        if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-      }
-      return COOT_OK;
-    }
+    if (n == 0) return empty_heads(res, &heads, 1, stream);
     if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * popcount(heads))
       return fail(COOT_ERR_WORKSPACE, "reductions need a workspace (coot_workspace_size)");
   } else if (n == 0) {
@@ -957,25 +971,7 @@ coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens
   const int64_t n = n_elem(in[0]);
   if (total_heads > 0) {
     if (out_dev == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
-    if (n == 0) {
-      if (all_heads & (COOT_HEAD_MIN | COOT_HEAD_MAX)) return fail(COOT_ERR_EMPTY, "min/max of an empty object");
-      // sums and norms of nothing are 0, any() is 0, all() is 1
-      cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * total_heads, (cudaStream_t)stream);
-      if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-      int base = 0;
-      for (int k = 0; k < n_trees; ++k) {
-        if (spec.tree_heads[k] & COOT_HEAD_ALL) {
-          const double* one = nullptr;
-          coot_status s = device_one(&one);
-          if (s != COOT_OK) return s;
-          e = cudaMemcpyAsync(out_dev + base + popcount(spec.tree_heads[k] & (COOT_HEAD_ALL - 1)), one, sizeof(double),
-                              cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
-          if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-        }
-        base += popcount(spec.tree_heads[k]);
-      }
-      return COOT_OK;
-    }
+    if (n == 0) return empty_heads(out_dev, spec.tree_heads, n_trees, stream);
     if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * total_heads)
       return fail(COOT_ERR_WORKSPACE, "reductions need a workspace (coot_workspace_size)");
   } else if (n == 0) {

@@ -18,7 +18,8 @@ import json
 import statistics
 import sys
 
-from . import KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE, KIND_ROWSTATS, KIND_ROWSUM  # noqa: F401
+from . import (KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_MULTI, KIND_REDUCE,  # noqa: F401
+               KIND_ROWSTATS, KIND_ROWSUM)
 
 GRIDS = {
     KIND_MAP: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
@@ -30,6 +31,7 @@ GRIDS = {
     KIND_COLSTATS: dict(block=[128, 256, 512], vec=[0, 2], unroll=[2, 4, 8], blocks_per_sm=[0], split=[0, 1, 2, 4]),
     KIND_ROWSTATS: dict(block=[64, 128, 256], vec=[0, 2, 1], unroll=[2, 4, 8], blocks_per_sm=[0],
                         split=[0, 8, 16, 32]),
+    KIND_MULTI: dict(block=[128, 256, 512], vec=[0, 2, 1], unroll=[1, 2, 4, 8], blocks_per_sm=[0], split=[0]),
 }
 
 
