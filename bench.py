@@ -533,14 +533,19 @@ def run_coot(args):
             step_e2e_pipelined()
             stream.wait_stream(s_out)  # the step ends when its last copy has landed
 
-        ms_e2e = timed_e2e(step_e2e_pipelined_joined, (s_in, s_out))
-        e2e = {"value": round(world * STEP_BYTES / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
-               "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": 4 * MAT_BYTES,
-               "d2h_bytes_per_step": 2 * MAT_BYTES + 2 * N * 4 + 4 * 8 * K,
-               "mode": f"{K} column blocks pipelined on three streams (copy in, compute, copy out)",
-               "serial": {"value": round(world * STEP_BYTES / (ms_serial * 1e-3) / 1e9, 2),
-                          "ms_per_step": round(ms_serial, 3),
-                          "mode": "copy in, step, copy out on one stream"}}
+        ms_pipe = timed_e2e(step_e2e_pipelined_joined, (s_in, s_out))
+        # `value` is the one-stream step: about ten host calls a step, so it
+        # does not depend on how busy the host cores are; the pipelined step
+        # issues about a hundred and measured 538, 408 and 163 GB/s on
+        # boxes whose host cores were less or more loaded
+        e2e = {"value": round(world * STEP_BYTES / (ms_serial * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(ms_serial, 3), "h2d_bytes_per_step": 4 * MAT_BYTES,
+               "d2h_bytes_per_step": 2 * MAT_BYTES + 2 * N * 4 + 4 * 8,
+               "mode": "copy in, step, copy out on one stream",
+               "pipelined": {"value": round(world * STEP_BYTES / (ms_pipe * 1e-3) / 1e9, 2),
+                             "ms_per_step": round(ms_pipe, 3),
+                             "d2h_bytes_per_step": 2 * MAT_BYTES + 2 * N * 4 + 4 * 8 * K,
+                             "mode": f"{K} column blocks pipelined on three streams (copy in, compute, copy out)"}}
 
     peak, peak_kind = peaks()
     dom = max(names, key=lambda n: statistics.mean(per_call[n]))
