@@ -317,3 +317,20 @@ def test_views_of_one_matrix_alias_by_rows_and_columns():
     d = _abi.coot_mat()
     assert L.coot_diag(ctypes.byref(parent), -2, ctypes.byref(d)) == 0
     assert (d.n_rows, d.n_cols, d.ld, d.ptr - parent.ptr) == (1, 300, 1001, 2 * 4)
+
+
+def test_header_compiles_as_c99_and_cpp(tmp_path):
+    """include/coot.h is a plain C header: it compiles as pedantic C99 and
+    as C++17 with every warning on."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "coot.h"\nint main(void) { return coot_version() > 0 ? 0 : 1; }\n')
+    for cc, flags in (("gcc", ["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror"]),
+                      ("g++", ["-std=c++17", "-Wall", "-Wextra", "-Werror", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, *flags, "-I", os.path.join(root, "include"), "-c", str(src), "-o",
+                            str(tmp_path / f"use_{cc}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, (cc, r.stderr)
