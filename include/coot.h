@@ -367,7 +367,9 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_ma
  *                           (k < n_trees, 1 <= n_trees <= 4); each tree
  *                           reads the first tree_inputs(k) <= n_in operands
  *                           and all trees share tree 0's compute type;
- *   in[0 .. n_in)           the operands (equal shapes, 1 <= n_in <= 4);
+ *   in[0 .. n_in)           the operands (equal shapes, 1 <= n_in <= 4),
+ *                           every one read once whether a tree uses it or
+ *                           not;
  *   outs                    NULL, or n_trees matrices: tree k is stored
  *                           into outs[k] when outs[k].ptr is not NULL
  *                           (same shape; it may be identical to an input,
