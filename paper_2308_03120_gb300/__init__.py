@@ -159,26 +159,34 @@ def _ws(ws, rows):
 # ---------------------------------------------------------------- set-up / host-only
 
 def coot_init(device: int = 0, flags: int = 0) -> None:
+    """Bind the library to CUDA device `device` (the runtime set-up of
+    Section 3); every device call needs it first."""
     _abi.call("coot_init", device, flags)
 
 
 def coot_finalize() -> None:
+    """Drop the compiled-kernel cache and the device binding."""
     _abi.call("coot_finalize")
 
 
 def coot_workspace_size(max_rows: int) -> int:
+    """Bytes of workspace the reductions and sums need for operands of up to
+    `max_rows` rows (row sums keep partials per row)."""
     n = ctypes.c_size_t()
     _abi.call("coot_workspace_size", max_rows, ctypes.byref(n))
     return n.value
 
 
 def coot_tree_check(tree: bytes):
+    """Validate serialised tree bytes; returns (inputs, compute type code,
+    FNV-1a hash of the bytes)."""
     n_in, comp, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
     _abi.call("coot_tree_check", tree, len(tree), ctypes.byref(n_in), ctypes.byref(comp), ctypes.byref(h))
     return n_in.value, comp.value, h.value
 
 
 def coot_tree_source(tree: bytes, kind: int = 0) -> str:
+    """The CUDA source generated for a tree and kernel kind (host only)."""
     n = ctypes.c_size_t()
     _abi.call("coot_tree_source", tree, len(tree), kind, None, 0, ctypes.byref(n))
     buf = ctypes.create_string_buffer(n.value + 1)
@@ -188,6 +196,8 @@ def coot_tree_source(tree: bytes, kind: int = 0) -> str:
 
 def coot_tree_compile(tree: bytes, kind: int = 0, in_dtype: int = COOT_F32, out_dtype: int = COOT_F32,
                       heads: int = 0, arch: str = "sm_103a") -> int:
+    """Compile a tree's kernel with NVRTC for `arch` without loading it (no
+    GPU needed); returns the cubin size in bytes."""
     n = ctypes.c_size_t()
     _abi.call("coot_tree_compile", tree, len(tree), kind, in_dtype, out_dtype, heads, arch.encode(),
               ctypes.byref(n))
@@ -195,6 +205,8 @@ def coot_tree_compile(tree: bytes, kind: int = 0, in_dtype: int = COOT_F32, out_
 
 
 def coot_unfused_tmp_count(tree: bytes) -> int:
+    """Temporaries the unfused baseline needs for a tree (one per inner
+    node, reused once dead)."""
     n = ctypes.c_int()
     _abi.call("coot_unfused_tmp_count", tree, len(tree), ctypes.byref(n))
     return n.value
@@ -210,6 +222,9 @@ def _result(out_dev, n):
 
 
 def coot_expr_eval(tree: bytes, ins, out: Mat, ws=None, stream=None) -> None:
+    """out = tree(ins...) element-wise in one fused kernel, no temporaries
+    (delayed evaluation at assignment, Section 7).  `out` may be identical
+    to an input."""
     arr, n = _mats(ins)
     o = out.c()
     _abi.call("coot_expr_eval", tree, len(tree), arr, n, ctypes.byref(o), None, 0, _stream(stream))
@@ -251,6 +266,8 @@ def coot_expr_multi(trees, ins, outs=None, heads=None, out_dev=None, ws=None, st
 
 
 def coot_accu(tree: bytes, ins, out_dev=None, ws=None, stream=None):
+    """accu(tree(ins...)): the sum of every element (Table 5), one pass;
+    returns a 1-element FP64 device tensor."""
     arr, n = _mats(ins)
     w = _ws(ws, 0)
     res = _result(out_dev, 1)
@@ -260,6 +277,8 @@ def coot_accu(tree: bytes, ins, out_dev=None, ws=None, stream=None):
 
 
 def coot_sum_dim(tree: bytes, ins, dim: int, out: Mat, ws=None, stream=None) -> None:
+    """sum(tree(ins...), dim) into `out` (Table 6): dim 0 sums each column
+    (out is 1 x n_cols), dim 1 each row (out is n_rows x 1)."""
     arr, n = _mats(ins)
     w = _ws(ws, ins[0].n_rows if dim == 1 else 0)
     o = out.c()
@@ -267,6 +286,8 @@ def coot_sum_dim(tree: bytes, ins, dim: int, out: Mat, ws=None, stream=None) -> 
 
 
 def coot_dot(a: Mat, b: Mat, out_dev=None, ws=None, stream=None):
+    """dot(a, b) over equal element counts (Table 5); returns a 1-element
+    FP64 device tensor."""
     w = _ws(ws, 0)
     res = _result(out_dev, 1)
     ca, cb = a.c(), b.c()
@@ -287,6 +308,8 @@ def coot_norm(tree: bytes, ins, p, out_dev=None, ws=None, stream=None):
 
 
 def coot_minmax(tree: bytes, ins, out_dev=None, ws=None, stream=None):
+    """[min, max] over every element of tree(ins...) (Table 6); NaN
+    propagates; returns a 2-element FP64 device tensor."""
     arr, n = _mats(ins)
     w = _ws(ws, 0)
     res = _result(out_dev, 2)
@@ -318,6 +341,8 @@ def coot_stats_dim(tree: bytes, ins, dim: int, stats: int, outs, norm_type: int 
 
 
 def coot_unfused_eval(tree: bytes, ins, out: Mat, tmp=None, stream=None) -> None:
+    """The baseline: one kernel per tree node with HBM temporaries (the
+    apply() chain of Section 7), for measuring what fusion gains."""
     import torch
     arr, n = _mats(ins)
     k = coot_unfused_tmp_count(tree)
@@ -378,6 +403,8 @@ def coot_batch_plan(items, n_inputs: int, device="cuda"):
 
 def coot_expr_eval_batched(tree: bytes, in_dtypes, out_dtype: int, colsum_dtype: int, plan, n_items: int,
                            n_work: int, stream=None) -> None:
+    """One persistent launch over a batch plan (coot_batch_plan): every
+    item's element-wise output and column sums."""
     dts = (ctypes.c_int32 * 4)(*(list(in_dtypes) + [0] * (4 - len(in_dtypes))))
     _abi.call("coot_expr_eval_batched", tree, len(tree), dts, out_dtype, colsum_dtype,
               ctypes.c_void_p(plan.data_ptr()), n_items, n_work, _stream(stream))

@@ -31,6 +31,10 @@ _UNARY = ("neg", "abs", "exp", "log", "sqrt", "square", "log10", "sin", "cos", "
 
 
 class Expr:
+    """A node of an expression tree built with Armadillo's operators (Table
+    2): `+`, `-`, `%` (Schur product), `/`, scalar `*`, unary `-`, `abs()`,
+    `**`, and the relational operators.  `A * B` between two expressions is
+    a matrix product and raises.  `tree()` serialises the tree."""
     __slots__ = ("op", "args", "value")
 
     def __init__(self, op: str, args=(), value=None):
@@ -132,58 +136,72 @@ def var(k: int) -> Expr:
 
 
 def const(v: float) -> Expr:
+    """A constant leaf (stored as FP64, rounded to the compute type)."""
     return Expr("c", value=float(v))
 
 
 def exp(e):
+    """exp(e), element-wise (Table 7)."""
     return Expr("exp", (Expr._wrap(e),))
 
 
 def log(e):
+    """Natural log(e), element-wise (Table 7)."""
     return Expr("log", (Expr._wrap(e),))
 
 
 def sqrt(e):
+    """sqrt(e), element-wise (Table 7)."""
     return Expr("sqrt", (Expr._wrap(e),))
 
 
 def square(e):
+    """e * e, element-wise (Table 7)."""
     return Expr("square", (Expr._wrap(e),))
 
 
 def abs_(e):
+    """|e|, element-wise (Table 7)."""
     return Expr("abs", (Expr._wrap(e),))
 
 
 def pow_(a, b):
+    """pow(a, b), element-wise (Table 7)."""
     return Expr("pow", (Expr._wrap(a), Expr._wrap(b)))
 
 
 def log10(e):
+    """log10(e), element-wise (Table 7)."""
     return Expr("log10", (Expr._wrap(e),))
 
 
 def sin(e):
+    """sin(e), element-wise (Table 7)."""
     return Expr("sin", (Expr._wrap(e),))
 
 
 def cos(e):
+    """cos(e), element-wise (Table 7)."""
     return Expr("cos", (Expr._wrap(e),))
 
 
 def tan(e):
+    """tan(e), element-wise (Table 7)."""
     return Expr("tan", (Expr._wrap(e),))
 
 
 def asin(e):
+    """asin(e), element-wise (Table 7)."""
     return Expr("asin", (Expr._wrap(e),))
 
 
 def acos(e):
+    """acos(e), element-wise (Table 7)."""
     return Expr("acos", (Expr._wrap(e),))
 
 
 def atan(e):
+    """atan(e), element-wise (Table 7)."""
     return Expr("atan", (Expr._wrap(e),))
 
 
