@@ -1203,15 +1203,16 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.store = true;
   spec.vec = 4;
   spec.unroll = 2;
-  spec.block = 256;
-  // Shared memory: two buffers of COOT_BATCH_UNIT elements per input, plus
-  // the unit's values when they cannot overwrite input 0 in place (at most
-  // 2 x 4 x 2048 x 8 B + 16 KB, always within the 227 KB of a block)
+  spec.block = 224;  // consumer threads; the launch adds the producer warp
+  // Shared memory: two stages of COOT_BATCH_UNIT elements per input, each
+  // with the unit's values when they cannot overwrite input 0 in place, a
+  // 128-byte unit header and two mbarriers (at most 2 x (4 x 2048 x 8 B +
+  // 16 KB), always within the 227 KB of a block)
   const int real = t.compute == COOT_F64 ? 8 : 4;
   size_t buf = 0;
   for (int i = 0; i < t.n_inputs; ++i) buf += (size_t)COOT_BATCH_UNIT * (size_t)dtype_size(in_dtypes[i]);
   const size_t vals = dtype_size(in_dtypes[0]) == real ? 0 : (size_t)COOT_BATCH_UNIT * (size_t)real;
-  const size_t smem = 2 * buf + vals + 16 + 2 * sizeof(coot_batch_item) + 2 * 16;
+  const size_t smem = 2 * (buf + vals + sizeof(coot_batch_item) + 16 + 2 * 8);
   if (smem > 227u * 1024u) return fail(COOT_ERR_UNSUPPORTED, "batched: two units of the inputs exceed shared memory");
   // blocks per SM: as many as their shared memory allows (228 KB per SM, 1 KB
   // of it reserved per block), at most 4 (a sweep over units of 1024, 2048,
@@ -1221,11 +1222,11 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   l.blocks_per_sm = max_blocks;
   const Launch& o = g_override[KIND_BATCHED];
   if (o.block) {
-    spec.block = o.block;
+    spec.block = std::min(o.block, 992);
     if (o.unroll) spec.unroll = o.unroll;
     if (o.blocks_per_sm > 0 && o.blocks_per_sm <= max_blocks) l.blocks_per_sm = o.blocks_per_sm;
   }
-  l.block = spec.block;
+  l.block = spec.block + 32;
   l.unroll = spec.unroll;
   l.vec = spec.vec;
   const Compiled* c = nullptr;

@@ -140,18 +140,29 @@ __device__ __forceinline__ int coot_slot_off() {
   return o;
 }
 
-// Thread 0: read unit u's descriptor into (sit, swk) and, when it
-// qualifies, start the bulk copies of its inputs into buf; swk->pad
-// records whether it did.
-__device__ void coot_issue(const coot_params& p, coot_i64 u, unsigned char* buf, unsigned bar,
-                           coot_batch_item_d* sit, coot_work_d* swk) {
-  const coot_batch_item_d* items = (const coot_batch_item_d*)p.plan;
-  const coot_work_d* work = (const coot_work_d*)(items + p.split);
-  coot_work_d wk = work[u];
-  const coot_batch_item_d it = items[wk.item];
-  const coot_i64 R = it.n_rows, n = (coot_i64)wk.n_cols * R, b0 = (coot_i64)wk.col0 * R;
-  bool ok = n > 0 && n <= COOT_UNIT && (it.out == nullptr || it.ld_out == R);
-  unsigned tx = 0;
+// a stage's unit: its matrix descriptor and work-list entry (pad = 1 when
+// the unit's inputs are staged)
+struct coot_stage_hdr {
+  coot_batch_item_d it;
+  coot_work_d wk;
+};
+static_assert(sizeof(coot_batch_item_d) == 112 && sizeof(coot_stage_hdr) == 128, "stage header layout");
+
+// The producer warp: write unit (work entry wk, this lane's word iw of the
+// unit's matrix descriptor) into the header h; when the unit qualifies,
+// lane 0 starts the bulk copies of its inputs into buf, counted on the
+// full mbarrier bar, else it arrives on bar at once.  The consumers
+// released buf through its empty mbarrier; the proxy fence orders their
+// accesses before the copies.
+__device__ __forceinline__ void coot_stage_unit(const coot_params& p, int4 wk, unsigned long long iw, int lane,
+                                                coot_stage_hdr* h, unsigned char* buf, unsigned bar) {
+  if (lane < 14) ((unsigned long long*)&h->it)[lane] = iw;
+  __syncwarp();
+  if (lane == 0) {
+    const coot_batch_item_d& it = h->it;
+    const coot_i64 R = it.n_rows, n = (coot_i64)wk.z * R, b0 = (coot_i64)wk.y * R;
+    bool ok = n > 0 && n <= COOT_UNIT && (it.out == nullptr || it.ld_out == R);
+    unsigned tx = 0;
 #define COOT_CHECK_IN(I)                                                                    \
   if constexpr (I < COOT_NIN) {                                                             \
     typedef typename coot_st<coot_in_code<I>::S>::T T;                                      \
@@ -160,18 +171,17 @@ __device__ void coot_issue(const coot_params& p, coot_i64 u, unsigned char* buf,
     ok = ok && it.ld_in[I] == R && ((unsigned long long)src & 15ull) == 0 && bytes16 > 0;   \
     tx += bytes16;                                                                          \
   }
-  COOT_CHECK_IN(0)
-  COOT_CHECK_IN(1)
-  COOT_CHECK_IN(2)
-  COOT_CHECK_IN(3)
+    COOT_CHECK_IN(0)
+    COOT_CHECK_IN(1)
+    COOT_CHECK_IN(2)
+    COOT_CHECK_IN(3)
 #undef COOT_CHECK_IN
-  wk.pad = ok ? 1 : 0;
-  *sit = it;
-  *swk = wk;
-  // p.n_cols == 1 is the status test: the unit is marked staged but no copy
-  // is started, so its wait runs out (nothing is in flight)
-  if (!ok || p.n_cols == 1) return;
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+    h->wk = coot_work_d{wk.x, wk.y, wk.z, ok ? 1 : 0};
+    // p.n_cols == 1 is the status test: the unit is marked staged but no
+    // copy is started, so its wait runs out (nothing is in flight)
+    if (ok && p.n_cols != 1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
 #define COOT_COPY_IN(I)                                                                     \
   if constexpr (I < COOT_NIN) {                                                             \
     typedef typename coot_st<coot_in_code<I>::S>::T T;                                      \
@@ -182,11 +192,17 @@ __device__ void coot_issue(const coot_params& p, coot_i64 u, unsigned char* buf,
         ::"r"(coot_smem_addr(buf + coot_slot_off<I>())), "l"(src), "r"(bytes16), "r"(bar)   \
         : "memory");                                                                        \
   }
-  COOT_COPY_IN(0)
-  COOT_COPY_IN(1)
-  COOT_COPY_IN(2)
-  COOT_COPY_IN(3)
+      COOT_COPY_IN(0)
+      COOT_COPY_IN(1)
+      COOT_COPY_IN(2)
+      COOT_COPY_IN(3)
 #undef COOT_COPY_IN
+    } else if (!ok) {
+      // read from global memory by the consumers: the header is all they wait for
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    }
+  }
+  __syncwarp();
 }
 
 // V consecutive elements of storage S at shared-memory address a (aligned
@@ -258,48 +274,90 @@ __device__ __forceinline__ void coot_load_staged(const unsigned char* buf, int e
 #undef COOT_LDS
 }
 
-extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 : 2)) COOT_ENTRY(const __grid_constant__ coot_params p) {
+// COOT_BLOCK consumer threads (COOT_WARPS warps) plus one producer warp per
+// block (launched with COOT_BLOCK + 32 threads); COOT_STAGES stages of
+// inputs in shared memory, each with a `full` mbarrier (the producer's
+// arrival and the copied bytes) and an `empty` one (one arrival per
+// consumer warp).  The consumers synchronise among themselves once per
+// unit (a named barrier before the column sums) and release a stage with
+// a non-blocking arrival, so a warp done with a unit's column sums goes on
+// to the next unit while others finish theirs.
+#define COOT_STAGES 2
+extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <= 256 ? 4 : 2))
+    COOT_ENTRY(const __grid_constant__ coot_params p) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  unsigned char* bufs = dsm;                                           // 2 x COOT_BUF_BYTES
-  COOT_REAL* vals_sep = (COOT_REAL*)(dsm + 2 * COOT_BUF_BYTES);         // COOT_UNIT values unless in place
-  unsigned long long* bars = (unsigned long long*)(dsm + 2 * COOT_BUF_BYTES +
-                                                   (COOT_VALS_IN_PLACE ? 0 : COOT_UNIT * sizeof(COOT_REAL)));
-  coot_batch_item_d* sit = (coot_batch_item_d*)(bars + 2);
-  coot_work_d* swk = (coot_work_d*)(sit + 2);
+  unsigned char* bufs = dsm;                                                   // COOT_STAGES x COOT_BUF_BYTES
+  COOT_REAL* vals_sep = (COOT_REAL*)(dsm + COOT_STAGES * COOT_BUF_BYTES);      // per stage, unless in place
+  coot_stage_hdr* hdr = (coot_stage_hdr*)(dsm + COOT_STAGES * COOT_BUF_BYTES +
+                                          (COOT_VALS_IN_PLACE ? 0 : COOT_STAGES * COOT_UNIT * sizeof(COOT_REAL)));
+  unsigned long long* full = (unsigned long long*)(hdr + COOT_STAGES);
+  unsigned long long* empty = full + COOT_STAGES;
   typedef typename coot_st<COOT_TO>::T TO;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool sum64 = p.rows_per_split == 3;
-  const unsigned bar0 = coot_smem_addr(bars), bar1 = coot_smem_addr(bars + 1);
+  const coot_i64 G = gridDim.x;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (blockIdx.x < p.n_work) coot_issue(p, blockIdx.x, bufs, bar0, sit, swk);
-  }
-  __syncthreads();
-  unsigned phases = 0u;  // bit s: the parity of buffer s's next phase
-  int b = 0;
-  for (coot_i64 w = blockIdx.x; w < p.n_work; w += gridDim.x, b ^= 1) {
-    // prefetch the next unit into the other buffer: the block finished with
-    // it at the barrier that ended the previous unit
-    if (threadIdx.x == 0 && w + gridDim.x < p.n_work) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      coot_issue(p, w + gridDim.x, bufs + (b ^ 1) * COOT_BUF_BYTES, b ? bar0 : bar1, sit + (b ^ 1), swk + (b ^ 1));
+    for (int k = 0; k < COOT_STAGES; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(coot_smem_addr(full + k)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(coot_smem_addr(empty + k)), "r"(COOT_WARPS)
+                   : "memory");
     }
-    const coot_batch_item_d it = sit[b];
-    const coot_work_d wk = swk[b];
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the only block-wide barrier
+  if (warp == 0) {
+    // ---- producer: stage the block's units in order, COOT_STAGES ahead of
+    // the consumers; the work entry and descriptor of each unit are loaded
+    // one unit before it is staged
+    const coot_batch_item_d* items = (const coot_batch_item_d*)p.plan;
+    const int4* work = (const int4*)(items + p.split);
+    const int4 zero4 = make_int4(0, 0, 0, 0);
+#define COOT_ITEM_WORD(w, u) \
+  ((u) < p.n_work && lane < 14 ? __ldg((const unsigned long long*)(items + (w).x) + lane) : 0ull)
+    const coot_i64 u0 = blockIdx.x;
+    int4 wk = u0 < p.n_work ? __ldg(work + u0) : zero4;
+    unsigned long long iw = COOT_ITEM_WORD(wk, u0);
+    int4 wn = u0 + G < p.n_work ? __ldg(work + u0 + G) : zero4;
+    unsigned eph = 0u;  // bit s: the parity of empty[s]'s next phase
+    int st = 0;
+    coot_i64 k = 0;
+    for (coot_i64 u = u0; u < p.n_work; u += G, ++k) {
+      if (k >= COOT_STAGES) {
+        const bool ok = __all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(empty + st), (eph >> st) & 1u));
+        if (!ok) {
+          if (lane == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
+          return;
+        }
+        eph ^= 1u << st;
+      }
+      coot_stage_unit(p, wk, iw, lane, &hdr[st], bufs + st * COOT_BUF_BYTES, coot_smem_addr(full + st));
+      iw = COOT_ITEM_WORD(wn, u + G);
+      wk = wn;
+      wn = u + 2 * G < p.n_work ? __ldg(work + u + 2 * G) : zero4;
+      st = st + 1 == COOT_STAGES ? 0 : st + 1;
+    }
+#undef COOT_ITEM_WORD
+    return;
+  }
+  // ---- consumers: thread ct of COOT_BLOCK, warp cw of COOT_WARPS
+  const int ct = (int)threadIdx.x - 32, cw = warp - 1;
+  unsigned fph = 0u;  // bit s: the parity of full[s]'s next phase
+  int st = 0;
+  for (coot_i64 w = blockIdx.x; w < p.n_work; w += G) {
+    if (!coot_mbar_wait(coot_smem_addr(full + st), (fph >> st) & 1u)) {
+      if (ct == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
+      return;
+    }
+    fph ^= 1u << st;
+    const coot_batch_item_d it = hdr[st].it;
+    const coot_work_d wk = hdr[st].wk;
     const coot_i64 R = it.n_rows;
     const coot_i64 c0 = wk.col0, nc = wk.n_cols;
     if (wk.pad) {
-      const unsigned char* buf = bufs + b * COOT_BUF_BYTES;
-      if (!coot_mbar_wait(b ? bar1 : bar0, (phases >> b) & 1u)) {
-        if (threadIdx.x == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
-        return;
-      }
-      phases ^= 1u << b;
+      const unsigned char* buf = bufs + st * COOT_BUF_BYTES;
       const int ni = (int)(nc * R);
       const coot_i64 b0 = c0 * R;
-      COOT_REAL* vals = COOT_VALS_IN_PLACE ? (COOT_REAL*)(bufs + b * COOT_BUF_BYTES) : vals_sep;
+      COOT_REAL* vals = COOT_VALS_IN_PLACE ? (COOT_REAL*)buf : vals_sep + st * COOT_UNIT;
       TO* out = it.out ? (TO*)it.out + b0 : (TO*)nullptr;
       // elements staged for every input
       int ns = ni;
@@ -315,7 +373,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
 #undef COOT_NS
       ns -= ns % COOT_VEC;
       const bool va = out == nullptr || coot_aligned16(out);
-      for (int e = (int)threadIdx.x * COOT_VEC; e < ns; e += COOT_BLOCK * COOT_VEC) {
+      for (int e = ct * COOT_VEC; e < ns; e += COOT_BLOCK * COOT_VEC) {
         COOT_REAL xv[4][COOT_VEC];
         coot_load_staged(buf, e, xv);
         COOT_REAL y[COOT_VEC];
@@ -344,7 +402,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
         COOT_SHIFT_T(2)
         COOT_SHIFT_T(3)
 #undef COOT_SHIFT_T
-        for (int e = ns + (int)threadIdx.x; e < ni; e += COOT_BLOCK) {
+        for (int e = ns + ct; e < ni; e += COOT_BLOCK) {
           COOT_REAL x[4];
           coot_load_flat(sh, e, x);
           const COOT_REAL y = coot_f(x);
@@ -353,7 +411,8 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
         }
       }
       if (it.colsum) {
-        __syncthreads();
+        // the consumer warps only: the producer never waits here
+        asm volatile("bar.sync 1, %0;" ::"n"(COOT_BLOCK) : "memory");
         // g lanes per column, g the largest power of two up to 32 that
         // leaves each lane 8 or more of the column's values (one lane per
         // column below 16 rows), 32 / g columns per warp pass.  Lane `sub`
@@ -366,7 +425,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
         while (g > 1 && g * 8 > Ri) g >>= 1;
         const int cpw = 32 / g, sub = lane & (g - 1);
         const int nch = (Ri + g - 1) / g;
-        for (int cb = warp * cpw; cb < nci; cb += COOT_WARPS * cpw) {
+        for (int cb = cw * cpw; cb < nci; cb += COOT_WARPS * cpw) {
           const int jj = cb + lane / g;
           COOT_REAL s = 0, c = 0;
           if (jj < nci) {
@@ -394,7 +453,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
       }
     } else {
       // strided, large or unaligned units: a warp per column from global memory
-      for (coot_i64 cj = warp; cj < nc; cj += COOT_WARPS) {
+      for (coot_i64 cj = cw; cj < nc; cj += COOT_WARPS) {
         const coot_i64 j = c0 + cj;
         COOT_REAL s = 0, c = 0;
         for (coot_i64 r0 = 0; r0 < R; r0 += 32 * COOT_UNROLL) {
@@ -422,7 +481,14 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, (COOT_BLOCK <= 256 ? 4 
         }
       }
     }
-    __syncthreads();  // buffer b and (sit, swk)[b] are free; the prefetch's descriptor is visible
+    // stage st is free for the producer once every consumer warp is done
+    // with it (the proxy fence orders this thread's accesses before the
+    // next bulk copies into it)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(coot_smem_addr(empty + st)) : "memory");
+    st = st + 1 == COOT_STAGES ? 0 : st + 1;
   }
 }
 #endif
