@@ -232,7 +232,9 @@ coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
  * vec: elements per vector access (1, 2, 4, 8; 0 = widest the operands'
  * alignment allows; a width they do not allow is lowered); unroll: vector
  * accesses in flight per thread and input, 1..16 (0 = built-in); for the
- * batched kind, rows in flight per lane; blocks_per_sm: cap on resident
+ * batched kind, `block` counts the computing threads (one staging warp is
+ * added to each block, up to 992 + 32) and `unroll` the rows in flight per
+ * lane of a unit read from global memory; blocks_per_sm: cap on resident
  * blocks per SM for the persistent grid (0 = occupancy limit); split:
  * column sums and statistics: segments per column, row sums and
  * statistics: column chunks (0 =
