@@ -334,3 +334,47 @@ def test_header_compiles_as_c99_and_cpp(tmp_path):
         r = subprocess.run([cc, *flags, "-I", os.path.join(root, "include"), "-c", str(src), "-o",
                             str(tmp_path / f"use_{cc}.o")], capture_output=True, text=True)
         assert r.returncode == 0, (cc, r.stderr)
+
+
+def test_batched_work_list_cuts_whole_aligned_columns():
+    """The batch plan (host only): items copied first, then one work unit
+    {item, col0, n_cols} per ~2048 elements of whole columns, cut so that a
+    unit of a 16-byte aligned FP32 matrix starts 16-byte aligned (col0 *
+    n_rows a multiple of 4); a column longer than 2048 rows is a unit of its
+    own."""
+    shapes = [(512, 9), (300, 13), (301, 11), (2, 5000), (3000, 3), (1, 1), (7, 0), (0, 6)]
+    items = []
+    for k, (r, c) in enumerate(shapes):
+        it = _abi.coot_batch_item()
+        for i in range(3):
+            it.in_[i] = (1 << 30) + (k << 24) + (i << 20)
+            it.ld_in[i] = max(r, 1)
+        it.ld_in[3] = max(r, 1)
+        it.out, it.ld_out = (1 << 40) + (k << 24), max(r, 1)
+        it.n_rows, it.n_cols = r, c
+        items.append(it)
+    arr = (_abi.coot_batch_item * len(items))(*items)
+    nbytes, n_work = ctypes.c_size_t(), ctypes.c_int64()
+    st, _ = _call("coot_batch_plan_size", arr, len(items), ctypes.byref(nbytes), ctypes.byref(n_work))
+    assert _abi.STATUS[st] == "COOT_OK"
+    buf = ctypes.create_string_buffer(nbytes.value)
+    st, _ = _call("coot_batch_plan_build", arr, len(items), 3, buf, nbytes.value)
+    assert _abi.STATUS[st] == "COOT_OK"
+    raw = buf.raw
+    assert raw[:112 * len(items)] == bytes(arr)  # the items, as given
+    units = [struct.unpack_from("<4i", raw, 112 * len(items) + 16 * u) for u in range(n_work.value)]
+    assert len(units) == n_work.value and nbytes.value == 112 * len(items) + 16 * len(units)
+    for k, (r, c) in enumerate(shapes):
+        mine = [(c0, nc) for item, c0, nc, _ in units if item == k]
+        # every column exactly once, in order, whole
+        cols = [c0 + j for c0, nc in mine for j in range(nc)]
+        assert cols == list(range(c)), (r, c, mine)
+        for c0, nc in mine:
+            assert nc * r <= 2048 or nc == 1, (r, c0, nc)
+            assert (c0 * r) % 4 == 0, (r, c0)  # aligned start
+        if c and r:
+            # whole-column units are as large as the rule allows
+            full = max(1, 2048 // r)
+            m = 1 if r % 4 == 0 else (2 if r % 2 == 0 else 4)
+            expect = full - full % m if full >= m else full
+            assert max(nc for _, nc in mine) == min(expect, c), (r, c, mine)
