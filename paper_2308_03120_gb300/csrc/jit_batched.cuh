@@ -82,27 +82,27 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // COOT_TO is the storage code of the element-wise outputs; the column sums
 // are stored in the storage code given by p.rows_per_split (0 FP32, 3 FP64).
 //
-// Up to four blocks per SM, each with two buffers of shared memory.  Thread
-// 0 copies the next dense unit's inputs into one buffer with bulk
-// asynchronous copies (cp.async.bulk, completion counted in bytes on an
-// mbarrier) while the block computes the current unit from the other: two
-// units of inputs are in flight or staged per SM without passing through
-// registers.  A unit qualifies when every operand is dense (its columns are
-// one contiguous run), it holds at most COOT_UNIT elements, and every input
-// run starts on a 16-byte boundary; the run's last bytes beyond a multiple of
-// 16 are read directly.
+// Up to four blocks per SM, each warp-specialised: a producer warp copies
+// the next dense units' inputs into a ring of shared-memory stages with bulk
+// asynchronous copies (cp.async.bulk, completion counted in bytes on the
+// stage's `full` mbarrier) while the consumer warps compute the current
+// unit from another stage.  A unit qualifies when every operand is dense
+// (its columns are one contiguous run), it holds at most COOT_UNIT
+// elements, and every input run starts on a 16-byte boundary; the run's
+// last bytes beyond a multiple of 16 are read directly.
 //
-// A staged unit: every thread takes COOT_VEC elements at a time from the
-// buffer (16-byte shared-memory accesses), writes the values and keeps them
-// in shared memory (over input 0 when the types allow); the column sums are
-// then taken from shared memory, a warp per column from 256 rows up and g
-// lanes per column below that (each lane adding 8 or more values, then a
-// double-word shuffle sum over the g lanes), each in a fixed order.  Other
-// units (strided, unaligned or too large): warp w of the block takes
-// columns w, w + warps, ... from global memory; lanes stride down the rows.
+// A staged unit: every consumer thread takes COOT_VEC elements at a time
+// from the stage (16-byte shared-memory accesses), writes the values and
+// keeps them in shared memory (over input 0 when the types allow); the
+// column sums are then taken from shared memory, a warp per column from 256
+// rows up and g lanes per column below that (each lane adding 8 or more
+// values, then a double-word shuffle sum over the g lanes), each in a fixed
+// order.  Other units (strided, unaligned or too large): consumer warp w
+// takes columns w, w + warps, ... from global memory; lanes stride down the
+// rows.
 //
 // Every wait on an mbarrier is bounded: a wait that gives up records
-// COOT_ERR_TIMEOUT in the status word (p.res) and the block returns.
+// COOT_ERR_TIMEOUT in the status word (p.res) and the warp returns.
 #define COOT_UNIT 2048
 template <int I>
 struct coot_in_bytes {
