@@ -378,3 +378,19 @@ def test_batched_work_list_cuts_whole_aligned_columns():
             m = 1 if r % 4 == 0 else (2 if r % 2 == 0 else 4)
             expect = full - full % m if full >= m else full
             assert max(nc for _, nc in mine) == min(expect, c), (r, c, mine)
+
+
+def test_several_tree_source_defines_every_slot():
+    """Kind 7 with one tree: coot_ft0 holds the tree, coot_ft1..3 are
+    constant stubs no code path reads, and the per-tree macros say one tree,
+    stored, with the given heads."""
+    t = serialize(synth.MAT_EXPR)
+    src = coot.coot_tree_source(t, 7)
+    assert "#define COOT_KIND 7" in src and "#define COOT_NT 1" in src
+    assert "#define COOT_ENTRY coot_multi" in src
+    body = src[src.index("COOT_REAL coot_ft0("):src.index("COOT_REAL coot_ft1(")]
+    assert "x[3]" in body and "fabsf(" in body
+    for k in (1, 2, 3):
+        assert f"COOT_REAL coot_ft{k}(const COOT_REAL* x) {{ return (COOT_REAL)0; }}" in src
+    assert "#define COOT_STORE_0 1" in src and "#define COOT_STORE_1 0" in src
+    assert "#define COOT_HEADS_1 0u" in src
