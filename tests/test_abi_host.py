@@ -247,6 +247,16 @@ def test_multi_tree_argument_errors():
     # heads need a workspace
     st, _ = call([t1, t2], heads=[1, 4], w=None, wb=0)
     assert _abi.STATUS[st] == "COOT_ERR_WORKSPACE"
+    # heads need a result pointer; 1 to 4 operands
+    keep = [ctypes.create_string_buffer(bytes(t1), len(t1))]
+    tp = (ctypes.c_void_p * 1)(ctypes.cast(keep[0], ctypes.c_void_p))
+    tl = (ctypes.c_size_t * 1)(len(t1))
+    h = (ctypes.c_uint * 1)(1)
+    st, msg = _call("coot_expr_multi", tp, tl, 1, ins, 2, None, h, None, ws, 1 << 22, None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and "result" in msg
+    for n_in in (0, 5):
+        st, _ = _call("coot_expr_multi", tp, tl, 1, ins, n_in, None, h, res, ws, 1 << 22, None)
+        assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
 
 
 def test_stats_argument_errors():
