@@ -573,9 +573,10 @@ coot_status coot_set_policy(int policy);
  * FP64 partial sums per row). */
 #define COOT_STATIC_MAX_ROWS 32768
 
-/* out = sum(a, 1), the sum of each row (Table 6), for an FP32 matrix a
- * (n_rows x n_cols, ld) into an FP32 n_rows x 1 out; allocates nothing.
- * n_rows > COOT_STATIC_MAX_ROWS returns COOT_ERR_UNSUPPORTED.  The first
+/* out = the sum of each row of an FP32 matrix a (n_rows x n_cols, ld),
+ * into an FP32 n_rows x 1 out; allocates nothing.  n_rows >
+ * COOT_STATIC_MAX_ROWS returns COOT_ERR_UNSUPPORTED; an out that overlaps a
+ * returns COOT_ERR_ALIAS.  The first
  * call on a device looks up the scratch's device address
  * (cudaGetSymbolAddress) for that device, with that device current; make
  * that first call before any stream capture.  Each call clears the

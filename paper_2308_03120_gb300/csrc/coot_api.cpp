@@ -135,6 +135,8 @@ static bool overlaps(const coot_mat& a, const coot_mat& b) {
   return row < a.n_rows && col < a.n_cols && col + b.n_cols > 0;
 }
 
+bool mats_overlap(const coot_mat& a, const coot_mat& b) { return overlaps(a, b); }
+
 // Output aliasing: identical to an input is allowed (and disables the
 // non-coherent load path), any other overlap is an error.
 static coot_status check_alias(const coot_mat& out, const coot_mat* in, int n_in, bool allow_identical, bool* aliased) {
@@ -1206,13 +1208,14 @@ coot_status coot_expr_eval_batched(const uint8_t* tree, size_t len, const int32_
   spec.block = 224;  // consumer threads; the launch adds the producer warp
   // Shared memory: two stages of COOT_BATCH_UNIT elements per input, each
   // with the unit's values when they cannot overwrite input 0 in place, a
-  // 128-byte unit header and two mbarriers (at most 2 x (4 x 2048 x 8 B +
-  // 16 KB), always within the 227 KB of a block)
+  // 128-byte unit header and two mbarriers, plus the consumers' mbarrier
+  // (at most 2 x (4 x 2048 x 8 B + 16 KB) + 16 B, always within the 227 KB
+  // of a block)
   const int real = t.compute == COOT_F64 ? 8 : 4;
   size_t buf = 0;
   for (int i = 0; i < t.n_inputs; ++i) buf += (size_t)COOT_BATCH_UNIT * (size_t)dtype_size(in_dtypes[i]);
   const size_t vals = dtype_size(in_dtypes[0]) == real ? 0 : (size_t)COOT_BATCH_UNIT * (size_t)real;
-  const size_t smem = 2 * (buf + vals + sizeof(coot_batch_item) + 16 + 2 * 8);
+  const size_t smem = 2 * (buf + vals + sizeof(coot_batch_item) + 16 + 2 * 8) + 16;
   if (smem > 227u * 1024u) return fail(COOT_ERR_UNSUPPORTED, "batched: two units of the inputs exceed shared memory");
   // blocks per SM: as many as their shared memory allows (228 KB per SM, 1 KB
   // of it reserved per block), at most 4 (a sweep over units of 1024, 2048,

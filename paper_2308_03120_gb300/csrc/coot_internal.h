@@ -17,6 +17,10 @@ namespace coot {
 coot_status fail(coot_status s, const std::string& msg);
 void clear_error();
 
+// Whether two matrices share an element (views of one parent are compared
+// by their row and column ranges; anything else by byte ranges).
+bool mats_overlap(const coot_mat& a, const coot_mat& b);
+
 // ------------------------------------------------------------ trees
 
 struct Node {

@@ -137,6 +137,9 @@ extern "C" coot_status coot_sum_rows_f32_static(const coot_mat* a, const coot_ma
   if (a->n_rows == 0) return COOT_OK;
   if ((a->ptr == nullptr && a->n_cols > 0) || out->ptr == nullptr)
     return coot::fail(COOT_ERR_INVALID_ARG, "NULL data pointer");
+  if (out->ld < 1) return coot::fail(COOT_ERR_INVALID_ARG, "bad output matrix");
+  // blocks write their rows of out while others may still read a's columns
+  if (coot::mats_overlap(*out, *a)) return coot::fail(COOT_ERR_ALIAS, "out overlaps a");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) return coot::fail(COOT_ERR_CUDA, "no current CUDA device");

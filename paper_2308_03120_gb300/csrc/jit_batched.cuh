@@ -101,8 +101,18 @@ __device__ __forceinline__ void coot_store_colsum(const coot_batch_item_d& it, c
 // takes columns w, w + warps, ... from global memory; lanes stride down the
 // rows.
 //
-// Every wait on an mbarrier is bounded: a wait that gives up records
-// COOT_ERR_TIMEOUT in the status word (p.res) and the warp returns.
+// Every wait in the kernel is bounded, and no thread waits at a barrier that
+// a thread which gave up could leave unfilled.  After the one block-wide
+// barrier at the start, threads meet only on mbarriers, each waited on with
+// a bounded try_wait: the consumers' `full` stages, the producer's `empty`
+// stages and the consumers' per-unit barrier `cons` (one arrival per
+// consumer warp).  Each warp votes on every wait's outcome (__all_sync), so
+// its lanes leave together and the warp-wide shuffles keep every lane.  A
+// warp that gives up records COOT_ERR_TIMEOUT in the status word (p.res)
+// and returns; the warps that depended on it then run out their own
+// bounded waits and return too.  Before the producer returns, by any path,
+// it waits (bounded) for the bulk copies it started, so no copy lands in
+// shared memory after the block has left.
 #define COOT_UNIT 2048
 template <int I>
 struct coot_in_bytes {
@@ -279,8 +289,9 @@ __device__ __forceinline__ void coot_load_staged(const unsigned char* buf, int e
 // inputs in shared memory, each with a `full` mbarrier (the producer's
 // arrival and the copied bytes) and an `empty` one (one arrival per
 // consumer warp).  The consumers synchronise among themselves once per
-// unit (a named barrier before the column sums) and release a stage with
-// a non-blocking arrival, so a warp done with a unit's column sums goes on
+// staged unit with column sums (the `cons` mbarrier, one arrival per
+// consumer warp, before the column sums) and release a stage with a
+// non-blocking arrival, so a warp done with a unit's column sums goes on
 // to the next unit while others finish theirs.
 #define COOT_STAGES 2
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <= 256 ? 4 : 2))
@@ -292,6 +303,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <
                                           (COOT_VALS_IN_PLACE ? 0 : COOT_STAGES * COOT_UNIT * sizeof(COOT_REAL)));
   unsigned long long* full = (unsigned long long*)(hdr + COOT_STAGES);
   unsigned long long* empty = full + COOT_STAGES;
+  unsigned long long* cons = empty + COOT_STAGES;
   typedef typename coot_st<COOT_TO>::T TO;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool sum64 = p.rows_per_split == 3;
@@ -302,6 +314,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(coot_smem_addr(empty + k)), "r"(COOT_WARPS)
                    : "memory");
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(coot_smem_addr(cons)), "r"(COOT_WARPS) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();  // the only block-wide barrier
@@ -319,33 +332,43 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <
     unsigned long long iw = COOT_ITEM_WORD(wk, u0);
     int4 wn = u0 + G < p.n_work ? __ldg(work + u0 + G) : zero4;
     unsigned eph = 0u;  // bit s: the parity of empty[s]'s next phase
+    unsigned fph = 0u;  // bit s: the parity of full[s]'s phase last armed
+    unsigned inflight = 0u;  // bit s: copies into stage s were started
+    bool ok = true;
     int st = 0;
     coot_i64 k = 0;
     for (coot_i64 u = u0; u < p.n_work; u += G, ++k) {
       if (k >= COOT_STAGES) {
-        const bool ok = __all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(empty + st), (eph >> st) & 1u));
-        if (!ok) {
-          if (lane == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
-          return;
-        }
+        ok = __all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(empty + st), (eph >> st) & 1u));
+        if (!ok) break;
         eph ^= 1u << st;
+        fph ^= 1u << st;  // full[st]'s previous phase completed before the consumers released it
       }
       coot_stage_unit(p, wk, iw, lane, &hdr[st], bufs + st * COOT_BUF_BYTES, coot_smem_addr(full + st));
+      // whether lane 0 started copies (the header's staged flag, on the
+      // normal path; the status test starts none)
+      if (hdr[st].wk.pad && p.n_cols != 1) inflight |= 1u << st; else inflight &= ~(1u << st);
       iw = COOT_ITEM_WORD(wn, u + G);
       wk = wn;
       wn = u + 2 * G < p.n_work ? __ldg(work + u + 2 * G) : zero4;
       st = st + 1 == COOT_STAGES ? 0 : st + 1;
     }
 #undef COOT_ITEM_WORD
+    // wait (bounded) for the copies still in flight: phase fph of full[s]
+    // completes once the stage's bytes have landed
+    for (int s = 0; s < COOT_STAGES; ++s)
+      if ((inflight >> s) & 1u) ok = __all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(full + s), (fph >> s) & 1u)) && ok;
+    if (!ok && lane == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
     return;
   }
   // ---- consumers: thread ct of COOT_BLOCK, warp cw of COOT_WARPS
   const int ct = (int)threadIdx.x - 32, cw = warp - 1;
   unsigned fph = 0u;  // bit s: the parity of full[s]'s next phase
+  unsigned cph = 0u;  // the parity of cons's next phase
   int st = 0;
   for (coot_i64 w = blockIdx.x; w < p.n_work; w += G) {
-    if (!coot_mbar_wait(coot_smem_addr(full + st), (fph >> st) & 1u)) {
-      if (ct == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
+    if (!__all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(full + st), (fph >> st) & 1u))) {
+      if (lane == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
       return;
     }
     fph ^= 1u << st;
@@ -411,8 +434,16 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK + 32, (COOT_BLOCK + 32 <
         }
       }
       if (it.colsum) {
-        // the consumer warps only: the producer never waits here
-        asm volatile("bar.sync 1, %0;" ::"n"(COOT_BLOCK) : "memory");
+        // the consumer warps only (the producer never waits here): each
+        // warp's values are in shared memory before its lane 0 arrives
+        // (release), and every lane's wait acquires the other warps' values
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(coot_smem_addr(cons)) : "memory");
+        if (!__all_sync(0xffffffffu, coot_mbar_wait(coot_smem_addr(cons), cph))) {
+          if (lane == 0 && p.res) atomicExch((unsigned*)p.res, 10u);  // COOT_ERR_TIMEOUT
+          return;
+        }
+        cph ^= 1u;
         // g lanes per column, g the largest power of two up to 32 that
         // leaves each lane 8 or more of the column's values (one lane per
         // column below 16 rows), 32 / g columns per warp pass.  Lane `sub`

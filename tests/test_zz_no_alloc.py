@@ -71,3 +71,18 @@ def test_static_row_sums_reject_too_many_rows():
     with pytest.raises(coot.CootError) as e:
         coot.coot_sum_rows_f32_static(coot.Mat(t, r, 1, r), coot.Mat(t, r, 1, r))
     assert e.value.status_name == "COOT_ERR_UNSUPPORTED" and "32768" in str(e.value)
+
+
+def test_static_row_sums_reject_an_overlapping_output():
+    # out placed over a's first column: blocks would write rows of out while
+    # other blocks still read that column
+    r, c = 1000, 8
+    t = torch.zeros(r * c + r, dtype=torch.float32, device="cuda")
+    a = coot.Mat(t[r:], r, c, r)
+    for start in (r, r + 17, r * c):
+        with pytest.raises(coot.CootError) as e:
+            coot.coot_sum_rows_f32_static(a, coot.Mat(t[start:start + r], r, 1, r))
+        assert e.value.status_name == "COOT_ERR_ALIAS"
+    # just before a: no shared element, accepted
+    coot.coot_sum_rows_f32_static(a, coot.Mat(t[:r], r, 1, r))
+    torch.cuda.synchronize()
