@@ -388,6 +388,22 @@ def run_coot(args):
     ms_one = _timed(torch, stream, g_one.replay, args.steps, args.warmup)
     one_bytes = (4 + 2 + 1 + 1) * MAT_BYTES
 
+    # every result of the step in ONE launch: both trees stored, the heads,
+    # and the column and row sums of `out` formed as it is computed
+    # (coot_expr_multi_dims): the inputs read once, nothing read back
+    dims_heads = [heads | coot.HEAD_COLSUM | coot.HEAD_ROWSUM, 0]
+
+    def step_one_launch(s=None):
+        coot.coot_expr_multi_dims([t_expr, t_chain], mats, [O1, O2], dims_heads, [COL, None], [ROW, None],
+                                  out_dev=res, ws=ws, stream=s)
+
+    g_launch = _graph(torch, step_one_launch)
+    ms_launch = _timed(torch, stream, g_launch.replay, args.steps, args.warmup)
+    coot.coot_expr_multi_dims([t_expr, t_chain], mats, [O1, O2], dims_heads, [COL, None], [ROW, None],
+                              out_dev=res, ws=ws)
+    launch_shape = shape_text(coot.coot_last_launch())
+    launch_bytes = (4 + 2) * MAT_BYTES + 2 * N * ELEM
+
     # unfused baseline of the same step: one kernel per node, temporaries in HBM
     ms_unfused = None
     if not args.no_unfused:
@@ -584,6 +600,12 @@ def run_coot(args):
                          "gbs": round(world * one_bytes / (ms_one * 1e-3) / 1e9, 1),
                          "algorithmic_bytes": one_bytes,
                          "calls": "coot_expr_multi (both trees, inputs read once) + two coot_sum_dim"},
+            "one_launch": {"ms_per_step": round(ms_launch, 4), "step_speedup": round(ms_step / ms_launch, 3),
+                           "gbs": round(world * launch_bytes / (ms_launch * 1e-3) / 1e9, 1),
+                           "frac": round(launch_bytes / (ms_launch * 1e-3) / 1e9 / peak, 4),
+                           "algorithmic_bytes": launch_bytes, "launch": launch_shape,
+                           "calls": "coot_expr_multi_dims: both trees stored, accu/norm2/min/max, sum dim 0 "
+                                    "and dim 1 of out, one kernel"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "traffic_note": traffic_note, "launch": shapes[dom],
@@ -975,7 +997,13 @@ def run_views(args):
             "one_pass": {"ms_per_step": round(ms_one, 4), "step_speedup": round(ms_step / ms_one, 3),
                          "gbs": round(world * one_bytes / (ms_one * 1e-3) / 1e9, 1),
                          "algorithmic_bytes": one_bytes,
-                         "calls": "coot_expr_multi (both trees, inputs read once) + two coot_sum_dim"}, "peak": peak, "peak_kind": peak_kind,
+                         "calls": "coot_expr_multi (both trees, inputs read once) + two coot_sum_dim"},
+            "one_launch": {"ms_per_step": round(ms_launch, 4), "step_speedup": round(ms_step / ms_launch, 3),
+                           "gbs": round(world * launch_bytes / (ms_launch * 1e-3) / 1e9, 1),
+                           "frac": round(launch_bytes / (ms_launch * 1e-3) / 1e9 / peak, 4),
+                           "algorithmic_bytes": launch_bytes, "launch": launch_shape,
+                           "calls": "coot_expr_multi_dims: both trees stored, accu/norm2/min/max, sum dim 0 "
+                                    "and dim 1 of out, one kernel"}, "peak": peak, "peak_kind": peak_kind,
                       "l2": "inputs larger than L2, no flush"}), flush=True)
 
 

@@ -189,6 +189,10 @@ typedef enum coot_op {
 #define COOT_HEAD_ANY    (1u << 9) /* 1 if some element is nonzero, else 0
                                       (any, Table 5; 0 when there are none)  */
 #define COOT_HEAD_MASK   0x3FFu    /* every head bit                          */
+/* Sums along a dimension, formed in the same pass (coot_expr_multi_dims
+ * only; they write matrices, not out_dev entries): */
+#define COOT_HEAD_COLSUM (1u << 10) /* sum(A, 0), each column's sum (Table 6) */
+#define COOT_HEAD_ROWSUM (1u << 11) /* sum(A, 1), each row's sum (Table 6)    */
 
 /* norm(A, p) selectors (Table 5): p = 1, 2, or one of these. */
 #define COOT_NORM_INF (-1)
@@ -225,7 +229,9 @@ coot_status coot_workspace_size(int64_t max_rows, size_t* bytes);
 /* Launch shape of the kernels of one kind (0 element-wise / with heads,
  * 1 reductions only, 2 column sums, 3 row sums, 4 batched, 5 column
  * statistics, 6 row statistics, 7 several trees in one pass; row
- * statistics use at most 256 threads per block) for the calls
+ * statistics use at most 256 threads per block; 8 several trees with sums
+ * along a dimension, where unroll is the vectors per lane in a row segment
+ * and split the number of column chunks) for the calls
  * that follow ON THIS THREAD, for tuning and for the learned selection of
  * launch shapes (not in the paper).  block: threads per block, 64..1024 in
  * steps of 64, or 0 to drop the setting (back to the built-in choice);
@@ -295,8 +301,10 @@ coot_status coot_tree_compile(const uint8_t* tree, size_t tree_len, int kind, in
  * truncated to buf_len) and its full length to *len.  kind: 0 = element-wise
  * evaluation, 1 = full reduction, 2 = column sums, 3 = row sums,
  * 4 = batched evaluation, 5 / 6 = column / row statistics (all six),
- * 7 = the several-tree kernel with this one tree; every input and the
- * output FP32.  Host-only;
+ * 7 = the several-tree kernel with this one tree, 8 = the same with its
+ * column and row sums (coot_tree_compile: those of the COOT_HEAD_COLSUM /
+ * COOT_HEAD_ROWSUM bits of `heads`, both when neither is set); every input
+ * and the output FP32.  Host-only;
  * for inspection and tests. */
 coot_status coot_tree_source(const uint8_t* tree, size_t tree_len, int kind, char* buf,
                              size_t buf_len, size_t* len);
@@ -388,6 +396,30 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t tree_len, const coot_ma
 coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens, int n_trees,
                             const coot_mat* in, int n_in, const coot_mat* outs, const unsigned* heads,
                             double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* coot_expr_multi plus sums along a dimension (Table 6, sum(A, dim)) of any
+ * tree in the SAME pass, with no second read of a stored result (the
+ * delayed evaluation of Section 7 carried into the sums):
+ *   heads[k] may also hold COOT_HEAD_COLSUM and / or COOT_HEAD_ROWSUM;
+ *   colsums  NULL, or n_trees matrices: tree k's column sums go to the
+ *            1 x n_cols matrix colsums[k] (element j at ptr + j * ld) when
+ *            heads[k] has COOT_HEAD_COLSUM;
+ *   rowsums  NULL, or n_trees matrices: tree k's row sums go to the
+ *            n_rows x 1 matrix rowsums[k] when heads[k] has COOT_HEAD_ROWSUM.
+ * Sums are stored in a floating-point type (COOT_ERR_DTYPE otherwise),
+ * formed as compensated sums of the compute-type values combined in a fixed
+ * order, and rounded once, as coot_sum_dim's; an empty object gives zeros.
+ * A sum may not overlap an input, a stored tree or another sum
+ * (COOT_ERR_ALIAS).  out_dev holds the full heads as for coot_expr_multi.
+ * The workspace holds partial sums and arrival counters; when a shape's
+ * partials do not fit in it (more than about 16,000 columns with more than
+ * one row segment), the sums are formed by the column / row sum kernels
+ * before the pass that stores the trees: same results within rounding,
+ * the inputs read again. */
+coot_status coot_expr_multi_dims(const uint8_t* const* trees, const size_t* tree_lens, int n_trees,
+                                 const coot_mat* in, int n_in, const coot_mat* outs, const unsigned* heads,
+                                 double* out_dev, const coot_mat* colsums, const coot_mat* rowsums,
+                                 void* ws, size_t ws_bytes, void* stream);
 
 /* Submatrix views (Table 1: .rows(a, b), .cols(c, d), .submat(p, q, r, s),
  * .row(i), .col(j)): the view of rows r0..r1 and columns c0..c1, inclusive,

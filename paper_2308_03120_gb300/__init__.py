@@ -23,8 +23,8 @@ from . import _abi
 from ._abi import (COOT_BF16, COOT_F16, COOT_F32, COOT_F64, COOT_I32, COOT_NORM_FRO, COOT_NORM_INF, COOT_NORM_NEG_INF,
                    COOT_U32,
                    HEAD_ALL, HEAD_ANY, HEAD_MAX, HEAD_MAXABS, HEAD_MIN, HEAD_MINABS, HEAD_NORM2, HEAD_SUM,
-                   HEAD_SUMABS, HEAD_SUMSQ, KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM, KIND_MAP, KIND_REDUCE,
-                   KIND_MULTI, KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
+                   HEAD_SUMABS, HEAD_SUMSQ, HEAD_COLSUM, HEAD_ROWSUM, KIND_BATCHED, KIND_COLSTATS, KIND_COLSUM,
+                   KIND_DIMS, KIND_MAP, KIND_REDUCE, KIND_MULTI, KIND_ROWSTATS, KIND_ROWSUM, STAT_MAX, STAT_MEAN, STAT_MIN, STAT_STDDEV, STAT_SUM, STAT_VAR,
                    CootError, coot_mat)
 from .expr import (Expr, abs_, acos, asin, atan, const, cos, eq, exp, log, log10, ne, pow_, serialize, sin, sqrt,
                    square, tan, var)
@@ -32,7 +32,8 @@ from .expr import (Expr, abs_, acos, asin, atan, const, cos, eq, exp, log, log10
 __all__ = [
     "Mat", "Workspace", "CootError", "coot_init", "coot_finalize", "coot_workspace_size", "coot_tree_check",
     "coot_tree_source", "coot_tree_compile", "coot_expr_eval", "coot_accu", "coot_sum_dim", "coot_dot",
-    "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_expr_multi", "coot_unfused_eval",
+    "coot_norm", "coot_minmax", "coot_all_any", "coot_stats_dim", "coot_expr_reduce", "coot_expr_multi",
+    "coot_expr_multi_dims", "coot_unfused_eval",
     "coot_unfused_tmp_count", "Expr", "var", "const", "exp", "log", "sqrt", "square", "abs_", "eq", "ne",
     "pow_", "log10", "sin", "cos", "tan", "asin", "acos", "atan", "serialize",
     "batch_item", "coot_batch_plan", "coot_expr_eval_batched",
@@ -262,6 +263,33 @@ def coot_expr_multi(trees, ins, outs=None, heads=None, out_dev=None, ws=None, st
     w = _ws(ws, 0)
     _abi.call("coot_expr_multi", tp, tl, nt, arr, n, o_arr, h_arr,
               ctypes.c_void_p(res.data_ptr()) if res is not None else None, w.ptr, w.bytes, _stream(stream))
+    return res
+
+
+def coot_expr_multi_dims(trees, ins, outs=None, heads=None, colsums=None, rowsums=None, out_dev=None, ws=None,
+                         stream=None):
+    """coot_expr_multi plus sums along a dimension in the same pass: heads[k]
+    may hold HEAD_COLSUM (tree k's column sums into colsums[k], a 1 x n_cols
+    Mat) and HEAD_ROWSUM (its row sums into rowsums[k], an n_rows x 1 Mat).
+    Returns the FP64 device tensor of the full heads, or None without."""
+    nt = len(trees)
+    keep = [ctypes.create_string_buffer(bytes(t), len(t)) for t in trees]
+    tp = (ctypes.c_void_p * nt)(*[ctypes.cast(b, ctypes.c_void_p) for b in keep])
+    tl = (ctypes.c_size_t * nt)(*[len(t) for t in trees])
+    arr, n = _mats(ins)
+
+    def mats(ms):
+        if ms is None:
+            return None
+        return (coot_mat * nt)(*[m.c() if m is not None else coot_mat() for m in ms])
+    hs = list(heads) if heads is not None else [0] * nt
+    h_arr = (ctypes.c_uint * nt)(*hs)
+    total = sum(bin(h & 0x3FF).count("1") for h in hs)
+    res = _result(out_dev, total) if total else None
+    w = _ws(ws, ins[0].n_rows)
+    _abi.call("coot_expr_multi_dims", tp, tl, nt, arr, n, mats(outs), h_arr,
+              ctypes.c_void_p(res.data_ptr()) if res is not None else None, mats(colsums), mats(rowsums), w.ptr,
+              w.bytes, _stream(stream))
     return res
 
 

@@ -13,9 +13,10 @@ COOT_NORM_INF, COOT_NORM_NEG_INF, COOT_NORM_FRO = -1, -2, -3
 HEAD_SUM, HEAD_SUMSQ, HEAD_NORM2, HEAD_SUMABS = 1, 2, 4, 8
 HEAD_MIN, HEAD_MAX, HEAD_MINABS, HEAD_MAXABS = 16, 32, 64, 128
 HEAD_ALL, HEAD_ANY = 256, 512
+HEAD_COLSUM, HEAD_ROWSUM = 1024, 2048
 STAT_SUM, STAT_MEAN, STAT_VAR, STAT_STDDEV, STAT_MIN, STAT_MAX = 1, 2, 4, 8, 16, 32
 KIND_MAP, KIND_REDUCE, KIND_COLSUM, KIND_ROWSUM, KIND_BATCHED = 0, 1, 2, 3, 4
-KIND_COLSTATS, KIND_ROWSTATS, KIND_MULTI = 5, 6, 7
+KIND_COLSTATS, KIND_ROWSTATS, KIND_MULTI, KIND_DIMS = 5, 6, 7, 8
 
 STATUS = ["COOT_OK", "COOT_ERR_INVALID_ARG", "COOT_ERR_BAD_TREE", "COOT_ERR_SHAPE", "COOT_ERR_DTYPE",
           "COOT_ERR_ALIAS", "COOT_ERR_EMPTY", "COOT_ERR_UNSUPPORTED", "COOT_ERR_COMPILE", "COOT_ERR_CUDA",
@@ -59,6 +60,8 @@ SIGNATURES = {
     "coot_expr_reduce": (c_int, [_u8p, c_size_t, _matp, c_int, c_uint, _matp, _dp, c_void_p, c_size_t, c_void_p]),
     "coot_expr_multi": (c_int, [POINTER(c_void_p), POINTER(c_size_t), c_int, _matp, c_int, _matp, POINTER(c_uint),
                                 _dp, c_void_p, c_size_t, c_void_p]),
+    "coot_expr_multi_dims": (c_int, [POINTER(c_void_p), POINTER(c_size_t), c_int, _matp, c_int, _matp,
+                                     POINTER(c_uint), _dp, _matp, _matp, c_void_p, c_size_t, c_void_p]),
     "coot_unfused_tmp_count": (c_int, [_u8p, c_size_t, POINTER(c_int)]),
     "coot_unfused_eval": (c_int, [_u8p, c_size_t, _matp, c_int, _matp, c_void_p, c_size_t, c_void_p]),
 }

@@ -41,7 +41,7 @@ def cuda_home() -> str:
 
 
 JIT_SOURCES = ["jit_rt.cuh", "jit_map.cuh", "jit_colsum.cuh", "jit_rowsum.cuh", "jit_batched.cuh", "jit_stats.cuh",
-               "jit_multi.cuh"]
+               "jit_multi.cuh", "jit_dims.cuh"]
 
 
 def _embed_runtime() -> str:

@@ -226,7 +226,7 @@ struct Launch {
 
 // A launch shape set by the caller for the calls that follow on this
 // thread (tuning, learned selection); block == 0 means "not set".
-static thread_local Launch g_override[KIND_COUNT] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0},
+static thread_local Launch g_override[KIND_COUNT] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0},
                                                      {1, 1, 0}, {1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
 // The shape of the last launch on this thread.
 static thread_local Launch g_last;
@@ -723,7 +723,7 @@ int coot_version(void) { return 100; }
 
 coot_status coot_set_launch_config(int kind, int block, int vec, int unroll, int blocks_per_sm, int64_t split) {
   clear_error();
-  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..7");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..8");
   if (block == 0) {
     g_override[kind] = Launch{1, 1, 0};
     return COOT_OK;
@@ -760,8 +760,8 @@ coot_status coot_prepare(const uint8_t* tree, size_t len, int kind, const int32_
   if (s != COOT_OK) return s;
   canonical_in_place(&t);
   if (kind < 0 || kind >= KIND_COUNT || !dtypes) return fail(COOT_ERR_INVALID_ARG, "bad arguments");
-  if (kind == KIND_MULTI)
-    return fail(COOT_ERR_UNSUPPORTED, "the several-tree kernel is compiled by its first coot_expr_multi call");
+  if (kind == KIND_MULTI || kind == KIND_DIMS)
+    return fail(COOT_ERR_UNSUPPORTED, "the several-tree kernels are compiled by their first call");
   if (block < 64 || block > 1024 || block % 64) return fail(COOT_ERR_INVALID_ARG, "block must be 64..1024, a multiple of 64");
   if (!(vec == 1 || vec == 2 || vec == 4 || vec == 8) || unroll < 1 || unroll > 16)
     return fail(COOT_ERR_INVALID_ARG, "vec must be 1, 2, 4 or 8 and unroll 1..16");
@@ -840,20 +840,31 @@ coot_status coot_tree_check(const uint8_t* tree, size_t len, int* n_inputs, int*
 }
 
 static coot_status spec_for(const Tree& t, int kind, int in_dtype, int out_dtype, unsigned heads, KernelSpec* spec) {
-  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..7");
+  if (kind < 0 || kind >= KIND_COUNT) return fail(COOT_ERR_INVALID_ARG, "kind must be 0..8");
   if (dtype_size(in_dtype) == 0 || dtype_size(out_dtype) == 0) return fail(COOT_ERR_DTYPE, "unknown dtype");
   spec->kind = kind;
   for (int i = 0; i < 4; ++i) spec->in_dtype[i] = i < t.n_inputs ? in_dtype : 0;
   spec->out_dtype = out_dtype;
   spec->store = kind == KIND_MAP || kind == KIND_BATCHED;
   spec->heads = (kind == KIND_MAP || kind == KIND_REDUCE || kind == KIND_COLSTATS || kind == KIND_ROWSTATS) ? heads : 0;
-  if (kind == KIND_MULTI) {
-    // one tree, stored and reduced by `heads`
+  if (kind == KIND_MULTI || kind == KIND_DIMS) {
+    // one tree, stored and reduced by `heads` (and, for kind 8, its column
+    // and row sums, in FP64 for FP64 storage, else FP32)
     spec->store = false;
     spec->n_trees = 1;
     spec->trees = &t;
     spec->tree_heads[0] = heads;
     spec->tree_out[0] = out_dtype;
+    if (kind == KIND_DIMS) {
+      // the dimension bits of `heads` (both when neither is given)
+      unsigned dims = heads & (COOT_HEAD_COLSUM | COOT_HEAD_ROWSUM);
+      if (dims == 0) dims = COOT_HEAD_COLSUM | COOT_HEAD_ROWSUM;
+      spec->tree_heads[0] = heads | dims;
+      const int sum_dt = out_dtype == COOT_F64 ? COOT_F64 : COOT_F32;
+      if (dims & COOT_HEAD_COLSUM) spec->tree_cs[0] = sum_dt;
+      if (dims & COOT_HEAD_ROWSUM) spec->tree_rs[0] = sum_dt;
+      spec->min_blocks = 2;
+    }
   }
   spec->vec = std::max(1, 16 / std::max(dtype_size(in_dtype), dtype_size(out_dtype)));
   spec->unroll = 2;
@@ -914,10 +925,21 @@ coot_status coot_expr_reduce(const uint8_t* tree, size_t len, const coot_mat* in
   return run_map_reduce(o.t, o.in, o.n, heads, out, out_dev, ws, ws_bytes, stream);
 }
 
-coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens, int n_trees, const coot_mat* in,
-                            int n_in, const coot_mat* outs, const unsigned* heads, double* out_dev, void* ws,
-                            size_t ws_bytes, void* stream) {
-  clear_error();
+// Trees, operands, stored outputs and heads of a several-tree call, checked
+// (shared by coot_expr_multi and coot_expr_multi_dims).
+struct MultiCall {
+  Tree ts[4];
+  KernelSpec spec;           // kind, trees, heads (with the dimension bits), stored types
+  const coot_mat* stored[4];
+  int n_stored = 0;
+  bool aliased = false;      // a stored tree is identical to an input
+  int total_heads = 0;       // full heads of every tree (one result each)
+  unsigned all_heads = 0;
+};
+
+static coot_status multi_check(const uint8_t* const* trees, const size_t* tree_lens, int n_trees, const coot_mat* in,
+                               int n_in, const coot_mat* outs, const unsigned* heads, unsigned allowed,
+                               MultiCall* mc) {
   if (trees == nullptr || tree_lens == nullptr || n_trees < 1 || n_trees > 4)
     return fail(COOT_ERR_INVALID_ARG, "1 to 4 trees");
   if (in == nullptr || n_in < 1 || n_in > COOT_TREE_MAX_INPUTS) return fail(COOT_ERR_INVALID_ARG, "1 to 4 inputs");
@@ -927,54 +949,56 @@ coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens
     if (in[i].n_rows != in[0].n_rows || in[i].n_cols != in[0].n_cols)
       return fail(COOT_ERR_SHAPE, "element-wise operands need equal sizes: input " + std::to_string(i));
   }
-  Tree ts[4];
-  const coot_mat* stored[4];
-  int n_stored = 0;
-  KernelSpec spec;
+  KernelSpec& spec = mc->spec;
   spec.kind = KIND_MULTI;
   spec.n_trees = n_trees;
-  spec.trees = ts;
-  unsigned all_heads = 0;
-  int total_heads = 0;
+  spec.trees = mc->ts;
   for (int k = 0; k < n_trees; ++k) {
     const std::string at = "tree " + std::to_string(k) + ": ";
-    coot_status s = parse_tree(trees[k], tree_lens[k], &ts[k]);
+    coot_status s = parse_tree(trees[k], tree_lens[k], &mc->ts[k]);
     if (s != COOT_OK) return fail(s, at + coot_last_error());
-    canonical_in_place(&ts[k]);
-    if (ts[k].n_inputs > n_in) return fail(COOT_ERR_INVALID_ARG, at + "uses more inputs than given");
-    if (ts[k].compute != ts[0].compute) return fail(COOT_ERR_DTYPE, at + "compute type differs from tree 0's");
+    canonical_in_place(&mc->ts[k]);
+    if (mc->ts[k].n_inputs > n_in) return fail(COOT_ERR_INVALID_ARG, at + "uses more inputs than given");
+    if (mc->ts[k].compute != mc->ts[0].compute) return fail(COOT_ERR_DTYPE, at + "compute type differs from tree 0's");
     const unsigned h = heads ? heads[k] : 0u;
-    if (h & ~COOT_HEAD_MASK) return fail(COOT_ERR_INVALID_ARG, at + "unknown head bits");
+    if (h & ~allowed) return fail(COOT_ERR_INVALID_ARG, at + "unknown head bits");
     spec.tree_heads[k] = h;
-    all_heads |= h;
-    total_heads += popcount(h);
+    mc->all_heads |= h;
+    mc->total_heads += popcount(h & COOT_HEAD_MASK);
     if (outs != nullptr && outs[k].ptr != nullptr) {
       s = check_mat(&outs[k], "output");
       if (s != COOT_OK) return fail(s, at + coot_last_error());
       if (outs[k].n_rows != in[0].n_rows || outs[k].n_cols != in[0].n_cols)
         return fail(COOT_ERR_SHAPE, at + "output shape differs from the operands'");
       spec.tree_out[k] = outs[k].dtype;
-      stored[n_stored++] = &outs[k];
+      mc->stored[mc->n_stored++] = &outs[k];
     } else if (h == 0) {
       return fail(COOT_ERR_INVALID_ARG, at + "nothing to compute (no output, no heads)");
     }
   }
   // outputs: each may be identical to an input (every element's inputs are
   // read before any tree's value is stored), none may overlap another
-  bool aliased = false;
-  for (int a = 0; a < n_stored; ++a) {
+  for (int a = 0; a < mc->n_stored; ++a) {
     bool al = false;
-    coot_status s = check_alias(*stored[a], in, n_in, true, &al);
+    coot_status s = check_alias(*mc->stored[a], in, n_in, true, &al);
     if (s != COOT_OK) return s;
-    aliased = aliased || al;
+    mc->aliased = mc->aliased || al;
     for (int b = 0; b < a; ++b)
-      if (overlaps(*stored[a], *stored[b])) return fail(COOT_ERR_ALIAS, "two stored trees overlap");
+      if (overlaps(*mc->stored[a], *mc->stored[b])) return fail(COOT_ERR_ALIAS, "two stored trees overlap");
   }
+  for (int i = 0; i < n_in; ++i) mc->spec.in_dtype[i] = in[i].dtype;
+  return COOT_OK;
+}
+
+// The several-tree kernel (kind 7) over a checked call.
+static coot_status run_multi(MultiCall& mc, const coot_mat* in, int n_in, double* out_dev, void* ws, size_t ws_bytes,
+                             void* stream) {
+  KernelSpec& spec = mc.spec;
   const int64_t n = n_elem(in[0]);
-  if (total_heads > 0) {
+  if (mc.total_heads > 0) {
     if (out_dev == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
-    if (n == 0) return empty_heads(out_dev, spec.tree_heads, n_trees, stream);
-    if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * total_heads)
+    if (n == 0) return empty_heads(out_dev, spec.tree_heads, spec.n_trees, stream);
+    if (ws == nullptr || ws_bytes < COOT_WS_PARTIALS_OFF + sizeof(double) * mc.total_heads)
       return fail(COOT_ERR_WORKSPACE, "reductions need a workspace (coot_workspace_size)");
   } else if (n == 0) {
     return COOT_OK;
@@ -982,23 +1006,23 @@ coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens
   // one launch: the synthetic tree carries the inputs and the compute type
   Tree t;
   t.n_inputs = n_in;
-  t.compute = ts[0].compute;
+  t.compute = mc.ts[0].compute;
   t.hash = 0;
-  const View v = make_view(in, n_in, nullptr, stored, n_stored);
-  CallInfo ci = call_info(KIND_MULTI, ts[0], in, n_in, n_stored ? stored[0]->dtype : -1, all_heads, v);
+  const View v = make_view(in, n_in, nullptr, mc.stored, mc.n_stored);
+  CallInfo ci = call_info(KIND_MULTI, mc.ts[0], in, n_in, mc.n_stored ? mc.stored[0]->dtype : -1, mc.all_heads, v);
   const Launch l = heuristic(KIND_MULTI, n_in, v, &ci);
-  for (int i = 0; i < n_in; ++i) spec.in_dtype[i] = in[i].dtype;
+  spec.kind = KIND_MULTI;
   spec.vec = l.vec;
   spec.unroll = l.unroll;
   spec.block = l.block;
-  spec.nc = !aliased;
+  spec.nc = !mc.aliased;
   const Compiled* c = nullptr;
   coot_status s = kernel_for(t, spec, &c);
   if (s != COOT_OK) return s;
   coot_multi_params_host mp;
   std::memset(&mp, 0, sizeof mp);
   fill_io(&mp.b, v, n_in);
-  for (int k = 0, j = 0; k < n_trees; ++k) {
+  for (int k = 0, j = 0; k < spec.n_trees; ++k) {
     if (spec.tree_out[k] < 0) continue;
     mp.out[k] = const_cast<void*>(v.ptr[n_in + j]);
     mp.ld_out[k] = v.ld[n_in + j];
@@ -1009,11 +1033,242 @@ coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens
   const int64_t tile = tile_rows(l);
   const int64_t units = ((v.n_rows + tile - 1) / tile) * v.n_cols;
   int64_t max_grid = INT32_MAX;
-  if (total_heads > 0) {
-    const int64_t fit = (int64_t)((ws_bytes - COOT_WS_PARTIALS_OFF) / (sizeof(double) * total_heads));
+  if (mc.total_heads > 0) {
+    const int64_t fit = (int64_t)((ws_bytes - COOT_WS_PARTIALS_OFF) / (sizeof(double) * mc.total_heads));
     max_grid = std::min<int64_t>(COOT_MAX_GRID, fit);
   }
   return launch(c, units, max_grid, l, &mp.b, stream, &mp);
+}
+
+coot_status coot_expr_multi(const uint8_t* const* trees, const size_t* tree_lens, int n_trees, const coot_mat* in,
+                            int n_in, const coot_mat* outs, const unsigned* heads, double* out_dev, void* ws,
+                            size_t ws_bytes, void* stream) {
+  clear_error();
+  MultiCall mc;
+  coot_status s = multi_check(trees, tree_lens, n_trees, in, n_in, outs, heads, COOT_HEAD_MASK, &mc);
+  if (s != COOT_OK) return s;
+  return run_multi(mc, in, n_in, out_dev, ws, ws_bytes, stream);
+}
+
+// Zeros into a 1 x n or n x 1 sum of an empty object (element k at
+// ptr + k * stride elements; every float type's zero is all-zero bits).
+static coot_status zero_sums(const coot_mat& m, void* stream) {
+  const int64_t n = n_elem(m);
+  if (n == 0) return COOT_OK;
+  const size_t es = dtype_size(m.dtype);
+  const int64_t stride = m.n_rows == 1 ? m.ld : 1;
+  cudaError_t e = stride == 1 ? cudaMemsetAsync(m.ptr, 0, es * n, (cudaStream_t)stream)
+                              : cudaMemset2DAsync(m.ptr, es * stride, 0, es, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(COOT_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+  return COOT_OK;
+}
+
+// The column / row sums of a several-tree call by the single-purpose
+// kernels (kinds 2 and 3, each reading the inputs again), then the stores
+// and full heads by the several-tree kernel: the route for shapes whose
+// partials do not fit the workspace.  The sums come first, so they read the
+// inputs before any stored tree can overwrite one.
+static coot_status run_dims_split(MultiCall& mc, const coot_mat* in, int n_in, const coot_mat* colsums,
+                                  const coot_mat* rowsums, double* out_dev, void* ws, size_t ws_bytes, void* stream) {
+  for (int k = 0; k < mc.spec.n_trees; ++k) {
+    const unsigned h = mc.spec.tree_heads[k];
+    const int nk = std::max(mc.ts[k].n_inputs, 1);
+    if (h & COOT_HEAD_COLSUM) {
+      coot_status s = run_sum_dim(mc.ts[k], in, nk, 0, &colsums[k], ws, ws_bytes, stream);
+      if (s != COOT_OK) return s;
+    }
+    if (h & COOT_HEAD_ROWSUM) {
+      coot_status s = run_sum_dim(mc.ts[k], in, nk, 1, &rowsums[k], ws, ws_bytes, stream);
+      if (s != COOT_OK) return s;
+    }
+  }
+  // the trees with something left to do, in order (their heads keep their
+  // places in out_dev: a tree without full heads adds none)
+  MultiCall rest;
+  int m = 0;
+  for (int k = 0; k < mc.spec.n_trees; ++k) {
+    const unsigned h = mc.spec.tree_heads[k] & COOT_HEAD_MASK;
+    if (h == 0 && mc.spec.tree_out[k] < 0) continue;
+    rest.ts[m] = mc.ts[k];
+    rest.spec.tree_heads[m] = h;
+    rest.spec.tree_out[m] = mc.spec.tree_out[k];
+    rest.all_heads |= h;
+    rest.total_heads += popcount(h);
+    ++m;
+  }
+  if (m == 0) return COOT_OK;
+  rest.spec.n_trees = m;
+  rest.spec.trees = rest.ts;
+  for (int i = 0; i < n_in; ++i) rest.spec.in_dtype[i] = in[i].dtype;
+  for (int a = 0; a < mc.n_stored; ++a) rest.stored[a] = mc.stored[a];
+  rest.n_stored = mc.n_stored;
+  rest.aliased = mc.aliased;
+  return run_multi(rest, in, n_in, out_dev, ws, ws_bytes, stream);
+}
+
+coot_status coot_expr_multi_dims(const uint8_t* const* trees, const size_t* tree_lens, int n_trees,
+                                 const coot_mat* in, int n_in, const coot_mat* outs, const unsigned* heads,
+                                 double* out_dev, const coot_mat* colsums, const coot_mat* rowsums, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  clear_error();
+  MultiCall mc;
+  coot_status s = multi_check(trees, tree_lens, n_trees, in, n_in, outs, heads,
+                              COOT_HEAD_MASK | COOT_HEAD_COLSUM | COOT_HEAD_ROWSUM, &mc);
+  if (s != COOT_OK) return s;
+  const int64_t R = in[0].n_rows, Cn = in[0].n_cols;
+  // the sums' outputs: shapes, float types, no overlap with any operand,
+  // stored tree or other sum
+  const coot_mat* sums[8];
+  int n_sums = 0, ncs = 0, nrs = 0;
+  for (int k = 0; k < n_trees; ++k) {
+    const std::string at = "tree " + std::to_string(k) + ": ";
+    const unsigned h = mc.spec.tree_heads[k];
+    for (int d = 0; d < 2; ++d) {
+      if (!(h & (d == 0 ? COOT_HEAD_COLSUM : COOT_HEAD_ROWSUM))) continue;
+      const coot_mat* arr = d == 0 ? colsums : rowsums;
+      if (arr == nullptr || arr[k].ptr == nullptr)
+        return fail(COOT_ERR_INVALID_ARG, at + (d == 0 ? "column" : "row") + " sums requested without an output");
+      const coot_mat& o = arr[k];
+      s = check_mat(&o, d == 0 ? "column sums" : "row sums");
+      if (s != COOT_OK) return fail(s, at + coot_last_error());
+      if (d == 0 ? (o.n_rows != 1 || o.n_cols != Cn) : (o.n_rows != R || o.n_cols != 1))
+        return fail(COOT_ERR_SHAPE, at + (d == 0 ? "column sums must be 1 x n_cols" : "row sums must be n_rows x 1"));
+      if (!is_float(o.dtype)) return fail(COOT_ERR_DTYPE, at + "sums are stored in a floating-point type");
+      bool al = false;
+      s = check_alias(o, in, n_in, false, &al);
+      if (s != COOT_OK) return fail(s, at + coot_last_error());
+      for (int a = 0; a < mc.n_stored; ++a)
+        if (overlaps(o, *mc.stored[a])) return fail(COOT_ERR_ALIAS, at + "a sum overlaps a stored tree");
+      for (int b = 0; b < n_sums; ++b)
+        if (overlaps(o, *sums[b])) return fail(COOT_ERR_ALIAS, at + "two sums overlap");
+      sums[n_sums++] = &o;
+      if (d == 0) {
+        mc.spec.tree_cs[k] = o.dtype;
+        ++ncs;
+      } else {
+        mc.spec.tree_rs[k] = o.dtype;
+        ++nrs;
+      }
+    }
+  }
+  if (ncs + nrs == 0) return run_multi(mc, in, n_in, out_dev, ws, ws_bytes, stream);
+  if (mc.total_heads > 0 && out_dev == nullptr) return fail(COOT_ERR_INVALID_ARG, "result pointer is NULL");
+  if (R == 0 || Cn == 0) {
+    for (int b = 0; b < n_sums; ++b) {
+      s = zero_sums(*sums[b], stream);
+      if (s != COOT_OK) return s;
+    }
+    return mc.total_heads > 0 ? empty_heads(out_dev, mc.spec.tree_heads, n_trees, stream) : COOT_OK;
+  }
+  if (ws == nullptr) return fail(COOT_ERR_WORKSPACE, "sums along a dimension need a workspace (coot_workspace_size)");
+
+  // ---- launch shape: warps on one row segment of 32 x vec x unroll rows,
+  // each warp a column at a time; the 2-D view (never flattened)
+  View v;
+  v.n_rows = R;
+  v.n_cols = Cn;
+  for (int i = 0; i < n_in; ++i) {
+    v.ptr[v.n] = in[i].ptr;
+    v.ld[v.n] = in[i].ld;
+    v.dtype[v.n] = in[i].dtype;
+    ++v.n;
+  }
+  for (int a = 0; a < mc.n_stored; ++a) {
+    v.ptr[v.n] = mc.stored[a]->ptr;
+    v.ld[v.n] = mc.stored[a]->ld;
+    v.dtype[v.n] = mc.stored[a]->dtype;
+    ++v.n;
+  }
+  const int real = mc.ts[0].compute == COOT_F64 ? 8 : 4;
+  Launch l;
+  l.block = 256;
+  l.vec = pick_vec(v);
+  l.unroll = 4;
+  const Launch& o = g_override[KIND_DIMS];
+  if (o.block) {
+    l.block = o.block;
+    if (o.vec) l.vec = pick_vec(v, o.vec);
+    if (o.unroll) l.unroll = o.unroll;
+    l.blocks_per_sm = o.blocks_per_sm;
+    l.split = o.split;
+  }
+  // no wider than the column needs; the row pairs of the block's warps fit
+  // 32 KB of shared memory
+  while (l.vec > 1 && 32 * l.vec > std::max<int64_t>(R, 32)) l.vec /= 2;
+  while (l.unroll > 1 && 32 * (int64_t)l.vec * (l.unroll - 1) >= R) --l.unroll;
+  // at most 16 values per lane and input in flight (more spill registers)
+  while (!o.unroll && l.unroll > 1 && l.vec * l.unroll > 16) --l.unroll;
+  if (nrs > 0)
+    while (l.unroll > 1 && (size_t)(l.block / 32) * 32 * l.vec * l.unroll * 2 * real > 32768) --l.unroll;
+  if (nrs > 0 && (size_t)(l.block / 32) * 32 * l.vec * l.unroll * 2 * real > 32768)
+    return run_dims_split(mc, in, n_in, colsums, rowsums, out_dev, ws, ws_bytes, stream);
+  const int64_t seg_rows = 32 * (int64_t)l.vec * l.unroll;
+  const int64_t n_seg = (R + seg_rows - 1) / seg_rows;
+  mc.spec.kind = KIND_DIMS;
+  mc.spec.vec = l.vec;
+  mc.spec.unroll = l.unroll;
+  mc.spec.block = l.block;
+  mc.spec.nc = !mc.aliased;
+  mc.spec.min_blocks = l.block <= 256 ? 2 : 1;
+  Tree t;
+  t.n_inputs = n_in;
+  t.compute = mc.ts[0].compute;
+  t.hash = 0;
+  const Compiled* c = nullptr;
+  s = kernel_for(t, mc.spec, &c);
+  if (s != COOT_OK) return s;
+  int bps = std::max(1, c->max_blocks_per_sm);
+  if (l.blocks_per_sm > 0) bps = std::min(bps, l.blocks_per_sm);
+  const int64_t resident = (int64_t)device().sm_count * bps;
+  // column chunks: enough units for every resident block, at most 64 (the
+  // row partials the workspace is sized for)
+  int64_t n_chunk = l.split > 0 ? l.split : std::max<int64_t>(1, (resident + n_seg - 1) / n_seg);
+  n_chunk = std::min<int64_t>(n_chunk, Cn);
+  if (nrs > 0) n_chunk = std::min<int64_t>(n_chunk, COOT_MAX_ROW_CHUNKS);
+  int64_t chunk_cols = (Cn + n_chunk - 1) / n_chunk;
+  n_chunk = (Cn + chunk_cols - 1) / chunk_cols;
+  // counters, partials and the workspace they need
+  const int64_t units = n_seg * n_chunk;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>({resident, units, (int64_t)COOT_MAX_GRID}));
+  auto round256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t head_bytes = round256(sizeof(double) * (size_t)grid * (size_t)mc.total_heads);
+  const size_t cpart = COOT_WS_PARTIALS_OFF + head_bytes;
+  const size_t cbytes = n_seg > 1 ? (size_t)ncs * 2 * (size_t)Cn * (size_t)n_seg * real : 0;
+  const size_t rpart = cpart + round256(cbytes);
+  auto rbytes = [&](int64_t nc) { return nc > 1 ? (size_t)nrs * 2 * (size_t)nc * (size_t)R * real : (size_t)0; };
+  while (n_chunk > 1 && rpart + rbytes(n_chunk) > ws_bytes) {
+    // fewer chunks: fewer row partials
+    n_chunk = std::max<int64_t>(1, n_chunk / 2);
+    chunk_cols = (Cn + n_chunk - 1) / n_chunk;
+    n_chunk = (Cn + chunk_cols - 1) / chunk_cols;
+  }
+  const int64_t counters = (ncs > 0 && n_seg > 1 ? Cn : 0) + (nrs > 0 && n_chunk > 1 ? n_seg : 0);
+  if (rpart + rbytes(n_chunk) > ws_bytes || counters > COOT_WS_MAX_COUNTERS)
+    return run_dims_split(mc, in, n_in, colsums, rowsums, out_dev, ws, ws_bytes, stream);
+  coot_dims_params_host dp;
+  std::memset(&dp, 0, sizeof dp);
+  fill_io(&dp.b, v, n_in);
+  for (int k = 0, j = 0; k < n_trees; ++k) {
+    if (mc.spec.tree_out[k] >= 0) {
+      dp.out[k] = const_cast<void*>(v.ptr[n_in + j]);
+      dp.ld_out[k] = v.ld[n_in + j];
+      ++j;
+    }
+    if (mc.spec.tree_cs[k] >= 0) {
+      dp.cs[k] = colsums[k].ptr;
+      dp.ld_cs[k] = colsums[k].ld;  // 1 x n_cols: element j at j * ld
+    }
+    if (mc.spec.tree_rs[k] >= 0) dp.rs[k] = rowsums[k].ptr;
+  }
+  dp.b.ws = (unsigned char*)ws;
+  dp.b.res = out_dev;
+  dp.b.split = n_chunk;
+  dp.n_seg = n_seg;
+  dp.n_chunk = n_chunk;
+  dp.chunk_cols = chunk_cols;
+  dp.cpart = (int64_t)cpart;
+  dp.rpart = (int64_t)rpart;
+  return launch(c, units, grid, l, &dp.b, stream, &dp);
 }
 
 coot_status coot_accu(const uint8_t* tree, size_t len, const coot_mat* in, int n_in, double* out_dev, void* ws,

@@ -49,7 +49,8 @@ enum Kind {
   KIND_COLSTATS = 5,
   KIND_ROWSTATS = 6,
   KIND_MULTI = 7,
-  KIND_COUNT = 8
+  KIND_DIMS = 8,
+  KIND_COUNT = 9
 };
 
 // Everything that selects one compiled kernel.
@@ -70,6 +71,12 @@ struct KernelSpec {
   const Tree* trees = nullptr;
   unsigned tree_heads[4] = {0, 0, 0, 0};
   int tree_out[4] = {-1, -1, -1, -1};
+  // several trees with sums along a dimension (KIND_DIMS): the storage code
+  // of tree t's column sums and row sums (-1 when not formed), and the
+  // launch bound's minimum of resident blocks per SM
+  int tree_cs[4] = {-1, -1, -1, -1};
+  int tree_rs[4] = {-1, -1, -1, -1};
+  int min_blocks = 1;
 };
 
 // Full CUDA source of one kernel: the prelude, the tree function and the
@@ -185,6 +192,23 @@ struct coot_multi_params_host {
   void* out[4];
   int64_t ld_out[4];
 };
+
+// Launch parameters of the kernel with sums along a dimension
+// (coot_dims_params in jit_dims.cuh).
+struct coot_dims_params_host {
+  coot_params_host b;
+  void* out[4];
+  int64_t ld_out[4];
+  void* cs[4];
+  int64_t ld_cs[4];
+  void* rs[4];
+  int64_t n_seg;
+  int64_t n_chunk;
+  int64_t chunk_cols;
+  int64_t cpart;
+  int64_t rpart;
+};
+static_assert(sizeof(coot_dims_params_host) == 8 * (18 + 25), "coot_dims_params layout");
 
 // Workspace layout (offsets in bytes), mirrored in jit_rt.cuh.
 #define COOT_WS_COUNTER_OFF 128

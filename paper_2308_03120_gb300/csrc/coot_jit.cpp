@@ -205,7 +205,9 @@ static uint64_t spec_key(const Tree& t, const KernelSpec& s) {
   const int64_t f[] = {s.kind, s.in_dtype[0], s.in_dtype[1], s.in_dtype[2], s.in_dtype[3], s.out_dtype,
                        s.store, (int64_t)s.heads, s.vec, s.unroll, s.block, s.nc, g_dev.id, s.n_trees,
                        (int64_t)s.tree_heads[0], (int64_t)s.tree_heads[1], (int64_t)s.tree_heads[2],
-                       (int64_t)s.tree_heads[3], s.tree_out[0], s.tree_out[1], s.tree_out[2], s.tree_out[3]};
+                       (int64_t)s.tree_heads[3], s.tree_out[0], s.tree_out[1], s.tree_out[2], s.tree_out[3],
+                       s.tree_cs[0], s.tree_cs[1], s.tree_cs[2], s.tree_cs[3], s.tree_rs[0], s.tree_rs[1],
+                       s.tree_rs[2], s.tree_rs[3], s.min_blocks};
   uint64_t h = t.hash;
   for (int k = 0; k < s.n_trees && s.trees; ++k) h = fnv1a(&s.trees[k].hash, sizeof s.trees[k].hash, h);
   return fnv1a(f, sizeof f, h);

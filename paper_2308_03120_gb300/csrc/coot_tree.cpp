@@ -167,6 +167,7 @@ const char* entry_name(const KernelSpec& spec) {
     case KIND_COLSTATS: return "coot_colstats";
     case KIND_ROWSTATS: return "coot_rowstats";
     case KIND_MULTI: return "coot_multi";
+    case KIND_DIMS: return "coot_dims";
     default: return "coot_batched";
   }
 }
@@ -187,10 +188,10 @@ std::string generate_source(const Tree& t, const KernelSpec& spec) {
                 spec.block,
                 spec.nc ? 1 : 0);
   std::string src(pre);
-  if (spec.kind == KIND_MULTI) {
+  if (spec.kind == KIND_MULTI || spec.kind == KIND_DIMS) {
     // several trees over the same inputs: coot_ft0 .. coot_ft3 (slots past
-    // n_trees hold a constant that no code path reads), each tree's heads,
-    // whether it is stored and its storage code
+    // n_trees hold a constant that no code path reads), each tree's full
+    // heads, whether it is stored and its storage code
     const int nt = spec.n_trees;
     char m[512];
     std::snprintf(m, sizeof m,
@@ -198,11 +199,30 @@ std::string generate_source(const Tree& t, const KernelSpec& spec) {
                   "#define COOT_HEADS_0 %uu\n#define COOT_HEADS_1 %uu\n#define COOT_HEADS_2 %uu\n#define COOT_HEADS_3 %uu\n"
                   "#define COOT_STORE_0 %d\n#define COOT_STORE_1 %d\n#define COOT_STORE_2 %d\n#define COOT_STORE_3 %d\n"
                   "#define COOT_TO_0 %d\n#define COOT_TO_1 %d\n#define COOT_TO_2 %d\n#define COOT_TO_3 %d\n",
-                  nt, spec.tree_heads[0], spec.tree_heads[1], spec.tree_heads[2], spec.tree_heads[3],
+                  nt, spec.tree_heads[0] & COOT_HEAD_MASK, spec.tree_heads[1] & COOT_HEAD_MASK,
+                  spec.tree_heads[2] & COOT_HEAD_MASK, spec.tree_heads[3] & COOT_HEAD_MASK,
                   spec.tree_out[0] >= 0, spec.tree_out[1] >= 0, spec.tree_out[2] >= 0, spec.tree_out[3] >= 0,
                   std::max(spec.tree_out[0], 0), std::max(spec.tree_out[1], 0), std::max(spec.tree_out[2], 0),
                   std::max(spec.tree_out[3], 0));
     src += m;
+    if (spec.kind == KIND_DIMS) {
+      // each tree's column and row sums (formed, storage code) and the
+      // launch bound
+      char d[512];
+      std::snprintf(d, sizeof d,
+                    "#define COOT_CS_0 %d\n#define COOT_CS_1 %d\n#define COOT_CS_2 %d\n#define COOT_CS_3 %d\n"
+                    "#define COOT_TCS_0 %d\n#define COOT_TCS_1 %d\n#define COOT_TCS_2 %d\n#define COOT_TCS_3 %d\n"
+                    "#define COOT_RS_0 %d\n#define COOT_RS_1 %d\n#define COOT_RS_2 %d\n#define COOT_RS_3 %d\n"
+                    "#define COOT_TRS_0 %d\n#define COOT_TRS_1 %d\n#define COOT_TRS_2 %d\n#define COOT_TRS_3 %d\n"
+                    "#define COOT_MINB %d\n",
+                    spec.tree_cs[0] >= 0, spec.tree_cs[1] >= 0, spec.tree_cs[2] >= 0, spec.tree_cs[3] >= 0,
+                    std::max(spec.tree_cs[0], 0), std::max(spec.tree_cs[1], 0), std::max(spec.tree_cs[2], 0),
+                    std::max(spec.tree_cs[3], 0),
+                    spec.tree_rs[0] >= 0, spec.tree_rs[1] >= 0, spec.tree_rs[2] >= 0, spec.tree_rs[3] >= 0,
+                    std::max(spec.tree_rs[0], 0), std::max(spec.tree_rs[1], 0), std::max(spec.tree_rs[2], 0),
+                    std::max(spec.tree_rs[3], 0), std::max(spec.min_blocks, 1));
+      src += d;
+    }
     for (int k = 0; k < 4; ++k) {
       const std::string name = "coot_ft" + std::to_string(k);
       if (k < nt && spec.trees) {

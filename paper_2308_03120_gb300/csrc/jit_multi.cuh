@@ -10,13 +10,7 @@
 // of all trees are combined as one list: tree 0's heads in bit order, then
 // tree 1's, and so on, into p.res.
 
-#if COOT_KIND == 7
-// Launch parameters (every field 8 bytes; mirrored on the host).
-struct coot_multi_params {
-  coot_params b;          // inputs, shape, workspace, results
-  void* out[4];           // stored trees (NULL when not stored)
-  coot_i64 ld_out[4];
-};
+#if COOT_KIND == 7 || COOT_KIND == 8
 
 #define COOT_MULTI_NH(H)                                                                         \
   ((((H) >> 0) & 1) + (((H) >> 1) & 1) + (((H) >> 2) & 1) + (((H) >> 3) & 1) + (((H) >> 4) & 1) + \
@@ -46,6 +40,16 @@ __device__ __forceinline__ void coot_multi_f(const COOT_REAL (&xv)[4][COOT_VEC],
     if constexpr (COOT_NT > 3) y[3][v] = coot_ft3(x);
   }
 }
+
+#endif
+
+#if COOT_KIND == 7
+// Launch parameters (every field 8 bytes; mirrored on the host).
+struct coot_multi_params {
+  coot_params b;          // inputs, shape, workspace, results
+  void* out[4];           // stored trees (NULL when not stored)
+  coot_i64 ld_out[4];
+};
 
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid_constant__ coot_multi_params mp) {
   const coot_params& p = mp.b;

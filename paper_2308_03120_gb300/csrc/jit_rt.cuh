@@ -7,7 +7,8 @@
 //   COOT_KIND     0 element-wise evaluation (optionally with reductions),
 //                 1 full reductions only, 2 column sums, 3 row sums,
 //                 4 batched evaluation over a work list, 5 column
-//                 statistics, 6 row statistics
+//                 statistics, 6 row statistics, 7 several trees in one
+//                 pass, 8 several trees with column / row sums
 //   COOT_NIN      number of input slots (1..4)
 //   COOT_TI0..3   storage code of each input (0 FP32, 1 BF16, 2 FP16, 3 FP64)
 //   COOT_TO       storage code of the stored output
@@ -691,7 +692,7 @@ __device__ __forceinline__ double coot_identity(unsigned bit) {
   return 0.0;
 }
 
-#if COOT_NHEADS > 0 || COOT_KIND == 7
+#if COOT_NHEADS > 0 || COOT_KIND == 7 || COOT_KIND == 8
 __device__ __forceinline__ COOT_REAL coot_identity_r(unsigned bit) {
   if (coot_min_head(bit)) return (COOT_REAL)COOT_INF_F;
   if (bit == COOT_HEAD_MAX || bit == COOT_HEAD_ANY) return -(COOT_REAL)COOT_INF_F;

@@ -160,6 +160,25 @@ def assert_sum_close(g: float, o: float, terms, errs, what=""):
     assert abs(g - o) <= tol, f"{what}: got {g!r}, oracle {o!r}, |diff| {abs(g - o):.3e} > tol {tol:.3e}"
 
 
+def check_dim_sums(tree: bytes, ins, dim: int, got: np.ndarray, what: str = ""):
+    """Sums along dim (0: each column, 1: each row), stored in FP32, against
+    the oracle's: the sum tolerance of each line over its terms, plus one
+    FP32 rounding of the result."""
+    v, bound, unsafe = O.error_bound(tree, ins)
+    assert not unsafe.any()
+    want = O.sum_dim(tree, ins, dim)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    terms = v if dim == 0 else v.T          # column k of `terms` feeds result k
+    errs = bound if dim == 0 else bound.T
+    s_abs = np.sum(np.abs(terms), axis=0)
+    tol = 1e-6 * np.abs(want) + np.where(np.abs(want) < 1e-3 * s_abs, 1e-9 * s_abs, 0.0)
+    tol += 6.0 * np.sqrt(np.sum(errs * errs, axis=0))
+    tol += np.abs(want) * 2.0 ** -24
+    bad = np.abs(got - want) > tol
+    assert not bad.any(), (what, dim, int(np.argmax(bad)), got[bad][:3], want[bad][:3])
+    return float(np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-300))) if want.size else 0.0
+
+
 def host_mats(specs, seed):
     """Seeded inputs: specs = [(dtype, n_rows, n_cols, ld, lo, hi)]."""
     out = []

@@ -121,13 +121,22 @@ def test_generated_source_inlines_the_tree():
     assert "exp(" in src64 and "#define COOT_REAL double" in src64
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("dt", [0, 1, 2, 3])
 def test_every_kernel_kind_compiles_for_sm103a(kind, dt):
     t = serialize(synth.MAT_CHAIN, compute="f64" if dt == 3 else "f32")
-    heads = {1: 0x3FF, 5: 0x3F, 6: 0x3F, 7: 0x3FF}.get(kind, 0)
-    out_dt = dt if kind < 5 else (3 if dt == 3 else 0)
+    heads = {1: 0x3FF, 5: 0x3F, 6: 0x3F, 7: 0x3FF, 8: 0x3FF}.get(kind, 0)
+    out_dt = dt if kind < 5 or kind >= 7 else (3 if dt == 3 else 0)
     n = coot.coot_tree_compile(t, kind=kind, in_dtype=dt, out_dtype=out_dt, heads=heads)
+    assert n > 1000
+
+
+@pytest.mark.parametrize("dims", [1 << 10, 1 << 11, 3 << 10])
+@pytest.mark.parametrize("heads", [0, 0x3FF])
+def test_dimension_sum_variants_compile(dims, heads):
+    """Kind 8 with column sums only, row sums only and both, with and
+    without full heads."""
+    n = coot.coot_tree_compile(serialize(synth.MAT_EXPR), kind=8, heads=heads | dims)
     assert n > 1000
 
 

@@ -95,13 +95,22 @@ def test_empty_is_a_no_op():
         out.check()
 
 
+# Random trees whose inputs put a few elements where the oracle's error
+# bound says nothing (a log/sqrt/division operand within its error of the
+# domain edge); those elements are skipped.  Every other tree is checked on
+# every element.  (Counts from the oracle's error_bound on these inputs.)
+RANDOM_TREE_SKIPS = {7: 3, 17: 3}
+
+
 @pytest.mark.parametrize("seed", range(24))
 def test_random_trees(seed):
     n_in = 1 + seed % 4
     e = synth.random_tree(500 + seed, 2 + seed % 11, n_in)
     r, c = (1 + 97 * seed) % 3001 + 1, 1 + seed % 5
     specs = [_f32(r, c, lo=-2.0, hi=2.0) for _ in range(n_in)]
-    _eval_case(e, specs, 900 + seed)
+    rep = _eval_case(e, specs, 900 + seed)
+    print(f"random tree {seed}: {rep['n']} elements, {rep['skipped']} skipped, max rel {rep.get('max_rel', 0):.2e}")
+    assert rep["skipped"] == RANDOM_TREE_SKIPS.get(seed, 0), rep
 
 
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
