@@ -1192,15 +1192,36 @@ coot_status coot_expr_multi_dims(const uint8_t* const* trees, const size_t* tree
     l.blocks_per_sm = o.blocks_per_sm;
     l.split = o.split;
   }
-  // no wider than the column needs; the row pairs of the block's warps fit
-  // 32 KB of shared memory
+  // no wider than the column needs
   while (l.vec > 1 && 32 * l.vec > std::max<int64_t>(R, 32)) l.vec /= 2;
   while (l.unroll > 1 && 32 * (int64_t)l.vec * (l.unroll - 1) >= R) --l.unroll;
-  // at most 16 values per lane and input in flight (more spill registers)
-  while (!o.unroll && l.unroll > 1 && l.vec * l.unroll > 16) --l.unroll;
-  if (nrs > 0)
-    while (l.unroll > 1 && (size_t)(l.block / 32) * 32 * l.vec * l.unroll * 2 * real > 32768) --l.unroll;
-  if (nrs > 0 && (size_t)(l.block / 32) * 32 * l.vec * l.unroll * 2 * real > 32768)
+  // at most 16 values per lane and input in flight; the next column's
+  // loads are issued before the current one is computed when both columns'
+  // values fit 32 registers each
+  const bool own_unroll = o.block != 0 && o.unroll != 0;
+  while (!own_unroll && l.unroll > 1 && l.vec * l.unroll > 16) --l.unroll;
+  const bool prefetch = n_in * l.vec * l.unroll <= 32;
+  // Each warp's shared memory (the kernel's COOT_WREG): its column tables
+  // (summed trees x CB columns x 33 lane entries of 2 values, CB the largest
+  // power of two up to 16 / trees for FP32, 8 / trees for FP64) or the row
+  // pairs of its segment (2 x 32 x vec x unroll values); the block's share
+  // stays within 44 KB of static shared memory.
+  int cb = (real == 4 ? 16 : 8) / std::max(ncs, 1);
+  for (int b = 16; b >= 1; b >>= 1)
+    if (cb >= b) {
+      cb = b;
+      break;
+    }
+  cb = std::max(cb, 1);
+  const size_t col_bytes = ncs > 0 ? (size_t)ncs * cb * 33 * 2 * real : 0;
+  auto warp_bytes = [&](const Launch& x) {
+    const size_t row_bytes = nrs > 0 ? (size_t)2 * 32 * x.vec * x.unroll * real : 0;
+    return std::max(col_bytes, row_bytes);
+  };
+  const size_t smem_cap = 44 * 1024;
+  while (l.unroll > 1 && (size_t)(l.block / 32) * warp_bytes(l) > smem_cap) --l.unroll;
+  while (l.block > 64 && (size_t)(l.block / 32) * warp_bytes(l) > smem_cap) l.block -= 64;
+  if ((size_t)(l.block / 32) * warp_bytes(l) > smem_cap)
     return run_dims_split(mc, in, n_in, colsums, rowsums, out_dev, ws, ws_bytes, stream);
   const int64_t seg_rows = 32 * (int64_t)l.vec * l.unroll;
   const int64_t n_seg = (R + seg_rows - 1) / seg_rows;
@@ -1210,6 +1231,7 @@ coot_status coot_expr_multi_dims(const uint8_t* const* trees, const size_t* tree
   mc.spec.block = l.block;
   mc.spec.nc = !mc.aliased;
   mc.spec.min_blocks = l.block <= 256 ? 2 : 1;
+  mc.spec.prefetch = prefetch ? 1 : 0;
   Tree t;
   t.n_inputs = n_in;
   t.compute = mc.ts[0].compute;
@@ -1221,10 +1243,25 @@ coot_status coot_expr_multi_dims(const uint8_t* const* trees, const size_t* tree
   if (l.blocks_per_sm > 0) bps = std::min(bps, l.blocks_per_sm);
   const int64_t resident = (int64_t)device().sm_count * bps;
   // column chunks: enough units for every resident block, at most 64 (the
-  // row partials the workspace is sized for)
-  int64_t n_chunk = l.split > 0 ? l.split : std::max<int64_t>(1, (resident + n_seg - 1) / n_seg);
-  n_chunk = std::min<int64_t>(n_chunk, Cn);
-  if (nrs > 0) n_chunk = std::min<int64_t>(n_chunk, COOT_MAX_ROW_CHUNKS);
+  // row partials the workspace is sized for); among up to twice that many,
+  // the count whose units fill the last wave of blocks best
+  const int64_t max_chunks = std::min<int64_t>(Cn, nrs > 0 ? COOT_MAX_ROW_CHUNKS : Cn);
+  int64_t n_chunk = std::max<int64_t>(1, (resident + n_seg - 1) / n_seg);
+  if (l.split > 0) {
+    n_chunk = l.split;
+  } else {
+    double best = 2.0;
+    const int64_t c0 = std::min(n_chunk, max_chunks);
+    for (int64_t c = c0; c <= std::min<int64_t>(2 * c0, max_chunks); ++c) {
+      const int64_t u = n_seg * c;
+      const double waste = (double)(((u + resident - 1) / resident) * resident - u) / (double)u;
+      if (waste < best - 1e-9) {
+        best = waste;
+        n_chunk = c;
+      }
+    }
+  }
+  n_chunk = std::min<int64_t>(n_chunk, max_chunks);
   int64_t chunk_cols = (Cn + n_chunk - 1) / n_chunk;
   n_chunk = (Cn + chunk_cols - 1) / chunk_cols;
   // counters, partials and the workspace they need

@@ -77,6 +77,7 @@ struct KernelSpec {
   int tree_cs[4] = {-1, -1, -1, -1};
   int tree_rs[4] = {-1, -1, -1, -1};
   int min_blocks = 1;
+  int prefetch = 0;  // KIND_DIMS: the next column's loads in flight during the current one's
 };
 
 // Full CUDA source of one kernel: the prelude, the tree function and the

@@ -207,7 +207,7 @@ static uint64_t spec_key(const Tree& t, const KernelSpec& s) {
                        (int64_t)s.tree_heads[0], (int64_t)s.tree_heads[1], (int64_t)s.tree_heads[2],
                        (int64_t)s.tree_heads[3], s.tree_out[0], s.tree_out[1], s.tree_out[2], s.tree_out[3],
                        s.tree_cs[0], s.tree_cs[1], s.tree_cs[2], s.tree_cs[3], s.tree_rs[0], s.tree_rs[1],
-                       s.tree_rs[2], s.tree_rs[3], s.min_blocks};
+                       s.tree_rs[2], s.tree_rs[3], s.min_blocks, s.prefetch};
   uint64_t h = t.hash;
   for (int k = 0; k < s.n_trees && s.trees; ++k) h = fnv1a(&s.trees[k].hash, sizeof s.trees[k].hash, h);
   return fnv1a(f, sizeof f, h);

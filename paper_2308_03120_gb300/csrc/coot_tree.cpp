@@ -214,13 +214,13 @@ std::string generate_source(const Tree& t, const KernelSpec& spec) {
                     "#define COOT_TCS_0 %d\n#define COOT_TCS_1 %d\n#define COOT_TCS_2 %d\n#define COOT_TCS_3 %d\n"
                     "#define COOT_RS_0 %d\n#define COOT_RS_1 %d\n#define COOT_RS_2 %d\n#define COOT_RS_3 %d\n"
                     "#define COOT_TRS_0 %d\n#define COOT_TRS_1 %d\n#define COOT_TRS_2 %d\n#define COOT_TRS_3 %d\n"
-                    "#define COOT_MINB %d\n",
+                    "#define COOT_MINB %d\n#define COOT_PREFETCH %d\n",
                     spec.tree_cs[0] >= 0, spec.tree_cs[1] >= 0, spec.tree_cs[2] >= 0, spec.tree_cs[3] >= 0,
                     std::max(spec.tree_cs[0], 0), std::max(spec.tree_cs[1], 0), std::max(spec.tree_cs[2], 0),
                     std::max(spec.tree_cs[3], 0),
                     spec.tree_rs[0] >= 0, spec.tree_rs[1] >= 0, spec.tree_rs[2] >= 0, spec.tree_rs[3] >= 0,
                     std::max(spec.tree_rs[0], 0), std::max(spec.tree_rs[1], 0), std::max(spec.tree_rs[2], 0),
-                    std::max(spec.tree_rs[3], 0), std::max(spec.min_blocks, 1));
+                    std::max(spec.tree_rs[3], 0), std::max(spec.min_blocks, 1), spec.prefetch ? 1 : 0);
       src += d;
     }
     for (int k = 0; k < 4; ++k) {

@@ -15,22 +15,32 @@
 // column every lane loads COOT_UNROLL vectors of COOT_VEC rows of every input
 // (32 lanes cover 32 * COOT_VEC consecutive rows per vector, so each warp
 // load is one contiguous run of the column), evaluates the trees, stores
-// them, feeds the full heads, and adds each value
-//   * to the lane's running pair for that row (TwoSum), and
-//   * to the lane's pair for the column (TwoSum), which a warp shuffle tree
-//     of double-word additions turns into the column's sum over the segment.
-// With one segment per column that is the column sum; otherwise the
-// segment's partial goes to the workspace and the last warp to finish a
-// column (arrival counter per column) adds the column's partials in segment
-// order.  At the end of a unit the warps' row pairs are added in warp order
-// in shared memory; with one chunk that is the row sum, otherwise the
+// them, feeds the full heads, and adds each value with TwoSum (two rows per
+// packed FP32-pair instruction)
+//   * to the lane's running pair for that row, and
+//   * to the lane's pair for the column.
+// Column sums.  A lane's column pair goes to the warp's shared-memory table
+// (a row of 32 lane pairs per column, COOT_CB columns per batch); once the
+// batch is full, lanes add the table's rows in lane order (COOT_CB entries
+// each, then a fixed xor-shuffle tree over the 32 / COOT_CB lanes of a
+// column), which gives each column's sum over the segment with a few
+// additions per value instead of a shuffle tree per column.  With one
+// segment per column that is the column sum; otherwise the segment's
+// partial goes to the workspace, and at the end of the unit (one fence per
+// warp) every column of the warp counts an arrival; the last lane to arrive
+// at a column adds the column's partials in segment order.
+// Row sums.  At the end of a unit the warps' row pairs are added in warp
+// order in shared memory; with one chunk that is the row sum, otherwise the
 // chunk's partial goes to the workspace and the last block to finish a
 // segment (counter per segment) adds the chunk partials in chunk order.
-// Every order is fixed, so the results do not depend on timing.
+// A tree whose plain sum (accu) is a head and whose row (else column) sums
+// are formed takes that head from the summed pairs instead of adding every
+// value a third time.  Every order is fixed, so the results do not depend
+// on timing.
 //
 // Workspace: the full heads' block partials at COOT_WS_PARTIALS_OFF (as in
-// every kernel with heads), the column partials at byte dp.cpart (high
-// parts, then low parts, per summed tree: n_cols x n_seg each) and the row
+// every kernel with heads), the column partials at byte dp.cpart (per summed
+// tree: n_cols x n_seg high parts, then as many low parts) and the row
 // partials at byte dp.rpart (per summed tree: n_chunk x n_rows high parts,
 // then low parts); column counters at COOT_WS_COUNTERS_OFF, then one
 // counter per segment.  The last arrival resets every counter it used.
@@ -54,8 +64,29 @@ struct coot_dims_params {
 #ifndef COOT_MINB
 #define COOT_MINB 1
 #endif
+#ifndef COOT_PREFETCH
+#define COOT_PREFETCH 0
+#endif
 #define COOT_NCS (COOT_CS_0 + COOT_CS_1 + COOT_CS_2 + COOT_CS_3)
 #define COOT_NRS (COOT_RS_0 + COOT_RS_1 + COOT_RS_2 + COOT_RS_3)
+#define COOT_NCS1 (COOT_NCS > 0 ? COOT_NCS : 1)
+#define COOT_NRS1 (COOT_NRS > 0 ? COOT_NRS : 1)
+// columns per batch of column reductions: the largest power of two up to
+// 16 (FP32) or 8 (FP64) per summed tree, so every table has the same bytes
+#define COOT_CB0 ((sizeof(COOT_REAL) == 4 ? 16 : 8) / COOT_NCS1)
+#define COOT_CB (COOT_CB0 >= 16 ? 16 : COOT_CB0 >= 8 ? 8 : COOT_CB0 >= 4 ? 4 : COOT_CB0 >= 2 ? 2 : 1)
+// values per lane and row added as packed FP32 pairs
+#define COOT_PACK (!COOT_REAL_F64 && (COOT_VEC % 2 == 0))
+#define COOT_RV (COOT_PACK ? COOT_VEC / 2 : COOT_VEC)
+#define COOT_RSTEP (COOT_PACK ? 2 : 1)
+// a table entry: a lane's column sum as {sum, compensation}
+#define COOT_ENT 2
+// each warp's shared memory: its column tables (COOT_CB columns x 33 lane
+// entries each), or (after its columns) its row pairs of one summed tree
+#define COOT_CTAB (COOT_CB * 33 * COOT_ENT)
+#define COOT_WREG_C (COOT_NCS > 0 ? COOT_NCS * COOT_CTAB : 0)
+#define COOT_WREG_R (COOT_NRS > 0 ? 2 * COOT_SEG : 0)
+#define COOT_WREG (COOT_WREG_C > COOT_WREG_R ? COOT_WREG_C : COOT_WREG_R)
 
 // index of tree t among the trees with column (row) sums
 template <int T> struct coot_cs_slot {
@@ -65,35 +96,86 @@ template <int T> struct coot_rs_slot {
   static constexpr int K = (T > 0 ? COOT_RS_0 : 0) + (T > 1 ? COOT_RS_1 : 0) + (T > 2 ? COOT_RS_2 : 0);
 };
 template <int T> struct coot_tree_flags;
-template <> struct coot_tree_flags<0> {
-  static constexpr bool CS = COOT_CS_0, RS = COOT_RS_0, ST = COOT_STORE_0;
-  static constexpr int TCS = COOT_TCS_0, TRS = COOT_TRS_0, TO = COOT_TO_0;
-};
-template <> struct coot_tree_flags<1> {
-  static constexpr bool CS = COOT_CS_1, RS = COOT_RS_1, ST = COOT_STORE_1;
-  static constexpr int TCS = COOT_TCS_1, TRS = COOT_TRS_1, TO = COOT_TO_1;
-};
-template <> struct coot_tree_flags<2> {
-  static constexpr bool CS = COOT_CS_2, RS = COOT_RS_2, ST = COOT_STORE_2;
-  static constexpr int TCS = COOT_TCS_2, TRS = COOT_TRS_2, TO = COOT_TO_2;
-};
-template <> struct coot_tree_flags<3> {
-  static constexpr bool CS = COOT_CS_3, RS = COOT_RS_3, ST = COOT_STORE_3;
-  static constexpr int TCS = COOT_TCS_3, TRS = COOT_TRS_3, TO = COOT_TO_3;
-};
+#define COOT_TREE_FLAGS(I)                                                                                   \
+  template <> struct coot_tree_flags<I> {                                                                    \
+    static constexpr bool CS = COOT_CS_##I, RS = COOT_RS_##I, ST = COOT_STORE_##I;                         \
+    static constexpr int TCS = COOT_TCS_##I, TRS = COOT_TRS_##I, TO = COOT_TO_##I;                         \
+    static constexpr unsigned H = COOT_HEADS_##I;                                                            \
+    /* the plain sum taken from the row (else column) pairs */                                               \
+    static constexpr bool SUM_ROWS = RS && (H & COOT_HEAD_SUM) != 0;                                         \
+    static constexpr bool SUM_COLS = !RS && CS && (H & COOT_HEAD_SUM) != 0;                                  \
+    static constexpr unsigned SKIP = (SUM_ROWS || SUM_COLS) ? COOT_HEAD_SUM : 0u;                            \
+  };
+COOT_TREE_FLAGS(0)
+COOT_TREE_FLAGS(1)
+COOT_TREE_FLAGS(2)
+COOT_TREE_FLAGS(3)
+#undef COOT_TREE_FLAGS
 
-// The warp's sum of double-word numbers, valid in every lane (xor-shuffle
-// tree of fixed shape; the double-word addition is commutative -- TwoSum's
-// pair does not depend on the order of its operands -- so both lanes of an
-// exchange form the same sum).
-__device__ __forceinline__ void coot_dw_warp_allsum(COOT_REAL& h, COOT_REAL& l) {
+// A running (sum, compensation) pair of values per lane: packed FP32 pairs
+// (two TwoSum lanes per instruction) or plain TwoSum.
+#if COOT_PACK
+typedef coot_f2 coot_racc;
+__device__ __forceinline__ void coot_racc_zero(coot_racc& a) { a = 0ull; }
+// x[0] enters lane 0, x[1] lane 1
+__device__ __forceinline__ void coot_racc_add(coot_racc& s, coot_racc& c, const COOT_REAL* x) {
+  coot_two_sum2(s, c, coot_pack(x[0], x[1]));
+}
+// the lanes as normalised double-word numbers: h[w], l[w] for w < COOT_RSTEP
+__device__ __forceinline__ void coot_racc_pairs(coot_racc s, coot_racc c, COOT_REAL* h, COOT_REAL* l) {
+  float sa, sb, ca, cb;
+  coot_unpack(s, sa, sb);
+  coot_unpack(c, ca, cb);
+  coot_dw_norm(sa, ca, h[0], l[0]);
+  coot_dw_norm(sb, cb, h[1], l[1]);
+}
+// the two lanes as one {sum, compensation}: the sums with TwoSum, the error
+// and both compensations added
+__device__ __forceinline__ void coot_racc_entry(coot_racc s2, coot_racc c2, COOT_REAL* out) {
+  float sa, sb, ca, cb;
+  coot_unpack(s2, sa, sb);
+  coot_unpack(c2, ca, cb);
+  float s = sa, c = ca;
+  coot_two_sum(s, c, sb);
+  out[0] = s;
+  out[1] = c + cb;
+}
+#else
+typedef COOT_REAL coot_racc;
+__device__ __forceinline__ void coot_racc_zero(coot_racc& a) { a = (COOT_REAL)0; }
+__device__ __forceinline__ void coot_racc_add(coot_racc& s, coot_racc& c, const COOT_REAL* x) {
+  coot_two_sum(s, c, x[0]);
+}
+__device__ __forceinline__ void coot_racc_pairs(coot_racc s, coot_racc c, COOT_REAL* h, COOT_REAL* l) {
+  coot_dw_norm(s, c, h[0], l[0]);
+}
+__device__ __forceinline__ void coot_racc_entry(coot_racc s, coot_racc c, COOT_REAL* out) {
+  out[0] = s;
+  out[1] = c;
+}
+#endif
+
+// The warp's sum over lanes that share a column: xor-shuffle tree over the
+// lane bits from `from` up (the double-word addition is commutative, so
+// both lanes of an exchange form the same sum).
+__device__ __forceinline__ void coot_dw_xor_sum(COOT_REAL& h, COOT_REAL& l, int from) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
+    if (o < from) break;
     const COOT_REAL yh = __shfl_xor_sync(0xffffffffu, h, o);
     const COOT_REAL yl = __shfl_xor_sync(0xffffffffu, l, o);
     coot_dw_add(h, l, yh, yl);
   }
 }
+
+// the plain sum of tree TT from a summed pair
+#define COOT_ADD_PAIR(TT, h, l)                                                                               \
+  {                                                                                                           \
+    if constexpr (TT == 0) acc0.add_pair(h, l);                                                               \
+    else if constexpr (TT == 1) acc1.add_pair(h, l);                                                          \
+    else if constexpr (TT == 2) acc2.add_pair(h, l);                                                          \
+    else acc3.add_pair(h, l);                                                                                 \
+  }
 
 extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(const __grid_constant__ coot_dims_params dp) {
   const coot_params& p = dp.b;
@@ -108,19 +190,23 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
   acc1.init();
   acc2.init();
   acc3.init();
+  __shared__ __align__(16) COOT_REAL wsm[COOT_WARPS][COOT_WREG];
 #if COOT_NRS > 0
-  // the warps' row pairs of one summed tree, added in warp order
-  __shared__ __align__(16) COOT_REAL red_h[COOT_WARPS][COOT_SEG];
-  __shared__ __align__(16) COOT_REAL red_l[COOT_WARPS][COOT_SEG];
   __shared__ int is_last;
 #endif
-  // this lane's row pairs: rows (k * 32 + lane) * VEC + v of the segment
-  // (declared without row sums too: the code that does not use them still
-  // names them)
-  COOT_REAL rsum[COOT_NRS > 0 ? COOT_NRS : 1][COOT_UNROLL][COOT_VEC];
-  COOT_REAL rcmp[COOT_NRS > 0 ? COOT_NRS : 1][COOT_UNROLL][COOT_VEC];
+  COOT_REAL* const mine = wsm[warp];
+  // this lane's row pairs: rows (k * 32 + lane) * VEC + q * RSTEP + w of the
+  // segment (declared without row sums too: the code that does not use them
+  // still names them)
+  coot_racc rsum[COOT_NRS1][COOT_UNROLL][COOT_RV];
+  coot_racc rcmp[COOT_NRS1][COOT_UNROLL][COOT_RV];
   coot_u32* cnt_col = (coot_u32*)(p.ws + COOT_WS_COUNTERS_OFF);
   coot_u32* cnt_seg = cnt_col + ((COOT_NCS > 0 && n_seg > 1) ? p.n_cols : 0);
+  COOT_REAL* const cph = (COOT_REAL*)(p.ws + dp.cpart);
+  const coot_i64 cper = p.n_cols * n_seg;
+  (void)cnt_seg;
+  (void)cph;
+  (void)cper;
 
   for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
     const coot_i64 chunk = u / n_seg;
@@ -129,174 +215,275 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
     const coot_i64 jb = chunk * dp.chunk_cols;
     const coot_i64 je = min(p.n_cols, jb + dp.chunk_cols);
     const bool whole = rb + COOT_SEG <= p.n_rows;
-#if COOT_NRS > 0
 #pragma unroll
-    for (int t = 0; t < COOT_NRS; ++t)
+    for (int t = 0; t < COOT_NRS1; ++t)
 #pragma unroll
       for (int k = 0; k < COOT_UNROLL; ++k)
 #pragma unroll
-        for (int v = 0; v < COOT_VEC; ++v) rsum[t][k][v] = rcmp[t][k][v] = (COOT_REAL)0;
-#endif
-    for (coot_i64 j = jb + warp; j < je; j += COOT_WARPS) {
-      COOT_REAL csum[COOT_NCS > 0 ? COOT_NCS : 1], ccmp[COOT_NCS > 0 ? COOT_NCS : 1];
-#pragma unroll
-      for (int t = 0; t < (COOT_NCS > 0 ? COOT_NCS : 1); ++t) csum[t] = ccmp[t] = (COOT_REAL)0;
-      // tree T's values y at rows (k, v) of this lane: stored, reduced,
-      // summed into the row and column pairs
-#define COOT_DIMS_USE(TT, k, row, yv, NV)                                                                      \
-  if constexpr (TT < COOT_NT) {                                                                                \
-    typedef coot_tree_flags<TT> F;                                                                             \
-    if constexpr (TT == 0) acc0.add_vec<NV>(yv); else if constexpr (TT == 1) acc1.add_vec<NV>(yv);              \
-    else if constexpr (TT == 2) acc2.add_vec<NV>(yv); else acc3.add_vec<NV>(yv);                               \
-    if constexpr (F::ST) {                                                                                    \
-      typedef typename coot_st<F::TO>::T TOT;                                                                 \
-      if constexpr (NV == COOT_VEC) coot_vstore<F::TO, COOT_VEC>((TOT*)dp.out[TT] + (j * dp.ld_out[TT] + (row)), yv); \
-      else coot_sstore<F::TO>((TOT*)dp.out[TT] + (j * dp.ld_out[TT] + (row)), yv[0]);                          \
-    }                                                                                                         \
-    if constexpr (F::RS) {                                                                                    \
-      _Pragma("unroll") for (int v = 0; v < NV; ++v)                                                         \
-        coot_two_sum(rsum[coot_rs_slot<TT>::K][k][v + vo], rcmp[coot_rs_slot<TT>::K][k][v + vo], yv[v]);      \
-    }                                                                                                         \
-    if constexpr (F::CS) {                                                                                    \
-      _Pragma("unroll") for (int v = 0; v < NV; ++v)                                                         \
-        coot_two_sum(csum[coot_cs_slot<TT>::K], ccmp[coot_cs_slot<TT>::K], yv[v]);                            \
-    }                                                                                                         \
-  }
-      if (whole) {
-        COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];
-#pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k) coot_load_vec(p, j, rb + ((coot_i64)k * 32 + lane) * COOT_VEC, xv[k]);
-#pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k) {
-          COOT_REAL y[4][COOT_VEC];
-          coot_multi_f(xv[k], y);
-          const coot_i64 row = rb + ((coot_i64)k * 32 + lane) * COOT_VEC;
-          constexpr int vo = 0;
-          COOT_DIMS_USE(0, k, row, y[0], COOT_VEC)
-          COOT_DIMS_USE(1, k, row, y[1], COOT_VEC)
-          COOT_DIMS_USE(2, k, row, y[2], COOT_VEC)
-          COOT_DIMS_USE(3, k, row, y[3], COOT_VEC)
+        for (int q = 0; q < COOT_RV; ++q) {
+          coot_racc_zero(rsum[t][k][q]);
+          coot_racc_zero(rcmp[t][k][q]);
         }
-      } else {
-        // the last, partial segment: whole vectors where they fit, then
-        // single elements
-#pragma unroll
-        for (int k = 0; k < COOT_UNROLL; ++k) {
-          const coot_i64 row0 = rb + ((coot_i64)k * 32 + lane) * COOT_VEC;
-          if (row0 + COOT_VEC <= p.n_rows) {
-            COOT_REAL xv[4][COOT_VEC];
-            coot_load_vec(p, j, row0, xv);
-            COOT_REAL y[4][COOT_VEC];
-            coot_multi_f(xv, y);
-            constexpr int vo = 0;
-            COOT_DIMS_USE(0, k, row0, y[0], COOT_VEC)
-            COOT_DIMS_USE(1, k, row0, y[1], COOT_VEC)
-            COOT_DIMS_USE(2, k, row0, y[2], COOT_VEC)
-            COOT_DIMS_USE(3, k, row0, y[3], COOT_VEC)
-          } else {
-#pragma unroll
-            for (int vo = 0; vo < COOT_VEC; ++vo) {
-              const coot_i64 row = row0 + vo;
-              if (row < p.n_rows) {
-                COOT_REAL x[4];
-                coot_load_one(p, j, row, x);
-                COOT_REAL y[4][1];
-                y[0][0] = coot_ft0(x);
-                if constexpr (COOT_NT > 1) y[1][0] = coot_ft1(x);
-                if constexpr (COOT_NT > 2) y[2][0] = coot_ft2(x);
-                if constexpr (COOT_NT > 3) y[3][0] = coot_ft3(x);
-                COOT_DIMS_USE(0, k, row, y[0], 1)
-                COOT_DIMS_USE(1, k, row, y[1], 1)
-                COOT_DIMS_USE(2, k, row, y[2], 1)
-                COOT_DIMS_USE(3, k, row, y[3], 1)
-              }
-            }
-          }
-        }
-      }
-#undef COOT_DIMS_USE
+    int nb = 0;            // columns in the current batch
+    coot_i64 jfirst = 0;   // the batch's first column (then every COOT_WARPS-th)
+    (void)jfirst;
+    // Column batch: each lane adds COOT_CB of a column's lane pairs, then
+    // the lanes of a column combine; the (column, segment) sums are stored
+    // or become partials.
+    auto flush = [&]() {
 #if COOT_NCS > 0
-      // the column's sum over the segment, in every lane
-      COOT_REAL ch[COOT_NCS], cl[COOT_NCS];
+      __syncwarp();
+      constexpr int G = 32 / COOT_CB;  // lanes per column
+      const int c = lane % COOT_CB, part = lane / COOT_CB;
+      const coot_i64 j = jfirst + (coot_i64)c * COOT_WARPS;
+      const bool mine_col = part == 0 && c < nb;
+      COOT_REAL ch[COOT_NCS1], cl[COOT_NCS1];
 #pragma unroll
       for (int t = 0; t < COOT_NCS; ++t) {
-        coot_dw_norm(csum[t], ccmp[t], ch[t], cl[t]);
-        coot_dw_warp_allsum(ch[t], cl[t]);
+        // lane entries part * CB .. part * CB + CB of column c, in order,
+        // into a running TwoSum pair (each entry's sums enter exactly, its
+        // compensations are added to the pair's)
+        COOT_REAL s = (COOT_REAL)0, e = (COOT_REAL)0;
+        if (c < nb) {
+          const COOT_REAL* tab = mine + t * COOT_CTAB + (c * 33 + part * COOT_CB) * COOT_ENT;
+#pragma unroll
+          for (int i = 0; i < COOT_CB; ++i) {
+            COOT_REAL en[COOT_ENT];
+#pragma unroll
+            for (int w = 0; w < COOT_ENT; ++w) en[w] = tab[i * COOT_ENT + w];
+            coot_two_sum(s, e, en[0]);
+            e += en[1];
+          }
+        }
+        coot_dw_norm(s, e, ch[t], cl[t]);
+        if constexpr (G > 1) coot_dw_xor_sum(ch[t], cl[t], COOT_CB);
       }
-      // column sum of tree T (summed-tree slot K) from the pair (h, l)
-#define COOT_CS_STORE(TT, h, l)                                                                                \
-  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::CS) {                                                     \
-    typedef typename coot_st<coot_tree_flags<TT>::TCS>::T TCT;                                                 \
-    ((TCT*)dp.cs[TT])[j * dp.ld_cs[TT]] = coot_dw_store<coot_tree_flags<TT>::TCS>(h[coot_cs_slot<TT>::K], l[coot_cs_slot<TT>::K]); \
+      __syncwarp();  // the tables are rewritten by the next batch
+      // the plain sum of a tree without row sums, from its column sums
+#define COOT_SUM_FROM_COLS(TT)                                                                                \
+  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::SUM_COLS) {                                              \
+    if (mine_col) COOT_ADD_PAIR(TT, ch[coot_cs_slot<TT>::K], cl[coot_cs_slot<TT>::K])                         \
+  }
+      COOT_SUM_FROM_COLS(0)
+      COOT_SUM_FROM_COLS(1)
+      COOT_SUM_FROM_COLS(2)
+      COOT_SUM_FROM_COLS(3)
+#undef COOT_SUM_FROM_COLS
+      // column sum of tree TT (summed-tree slot K) from the pair (h, l)
+#define COOT_CS_STORE(TT, h, l)                                                                               \
+  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::CS) {                                                   \
+    typedef typename coot_st<coot_tree_flags<TT>::TCS>::T TCT;                                                \
+    ((TCT*)dp.cs[TT])[j * dp.ld_cs[TT]] =                                                                     \
+        coot_dw_store<coot_tree_flags<TT>::TCS>(h[coot_cs_slot<TT>::K], l[coot_cs_slot<TT>::K]);             \
   }
       if (n_seg == 1) {
-        if (lane == 0) {
+        if (mine_col) {
           COOT_CS_STORE(0, ch, cl)
           COOT_CS_STORE(1, ch, cl)
           COOT_CS_STORE(2, ch, cl)
           COOT_CS_STORE(3, ch, cl)
         }
       } else {
-        // partials: tree slot t's high parts at [t][j][seg], then its low parts
-        COOT_REAL* ph = (COOT_REAL*)(p.ws + dp.cpart);
-        const coot_i64 per = p.n_cols * n_seg;
-        if (lane == 0) {
+        // partials: summed-tree slot t's high parts at [t][j][seg], then its
+        // low parts (made visible, and counted, at the end of the unit)
+        if (mine_col) {
 #pragma unroll
           for (int t = 0; t < COOT_NCS; ++t) {
-            ph[2 * t * per + j * n_seg + seg] = ch[t];
-            ph[(2 * t + 1) * per + j * n_seg + seg] = cl[t];
-          }
-          __threadfence();
-        }
-        unsigned last = 0;
-        if (lane == 0) last = atomicAdd(cnt_col + j, 1u) == (coot_u32)(n_seg - 1);
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-          __threadfence();
-          // lane q adds segments q, q + 32, ... in order; then the fixed tree
-          COOT_REAL sh[COOT_NCS], sl[COOT_NCS];
-#pragma unroll
-          for (int t = 0; t < COOT_NCS; ++t) {
-            sh[t] = sl[t] = (COOT_REAL)0;
-            for (coot_i64 q = lane; q < n_seg; q += 32)
-              coot_dw_add(sh[t], sl[t], __ldcg(ph + 2 * t * per + j * n_seg + q),
-                          __ldcg(ph + (2 * t + 1) * per + j * n_seg + q));
-            coot_dw_warp_allsum(sh[t], sl[t]);
-          }
-          if (lane == 0) {
-            COOT_CS_STORE(0, sh, sl)
-            COOT_CS_STORE(1, sh, sl)
-            COOT_CS_STORE(2, sh, sl)
-            COOT_CS_STORE(3, sh, sl)
-            cnt_col[j] = 0u;  // ready for the next call
+            cph[2 * t * cper + j * n_seg + seg] = ch[t];
+            cph[(2 * t + 1) * cper + j * n_seg + seg] = cl[t];
           }
         }
       }
 #undef COOT_CS_STORE
+      nb = 0;
 #endif
+    };
+
+    // The warp's columns (with COOT_PREFETCH, each one's inputs loaded
+    // while the previous one is computed, in two register buffers).  In the
+    // last, partial segment the vector that crosses the end is loaded
+    // element by element with 0 past the end, and the values of rows past
+    // the end are neither stored nor reduced.
+    COOT_REAL xa[COOT_UNROLL][4][COOT_VEC], xb[COOT_UNROLL][4][COOT_VEC];
+    auto load_col = [&](coot_i64 j, COOT_REAL (&x)[COOT_UNROLL][4][COOT_VEC]) {
+#pragma unroll
+      for (int k = 0; k < COOT_UNROLL; ++k) {
+        const coot_i64 row0 = rb + ((coot_i64)k * 32 + lane) * COOT_VEC;
+        if (whole || row0 + COOT_VEC <= p.n_rows) {
+          coot_load_vec(p, j, row0, x[k]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < COOT_VEC; ++v) {
+            COOT_REAL e[4] = {(COOT_REAL)0, (COOT_REAL)0, (COOT_REAL)0, (COOT_REAL)0};
+            if (row0 + v < p.n_rows) coot_load_one(p, j, row0 + v, e);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[k][i][v] = e[i];
+          }
+        }
+      }
+    };
+    // one column's values: stored, reduced, summed
+    auto process = [&](coot_i64 j, const COOT_REAL (&xc)[COOT_UNROLL][4][COOT_VEC]) {
+        if (nb == 0) jfirst = j;
+        coot_racc csum[COOT_NCS1], ccmp[COOT_NCS1];
+#pragma unroll
+        for (int t = 0; t < COOT_NCS1; ++t) {
+          coot_racc_zero(csum[t]);
+          coot_racc_zero(ccmp[t]);
+        }
+        // tree TT's COOT_VEC values yv at rows row .. row + VEC of this lane
+        // (vector k): stored, reduced, added to the row and column pairs; in
+        // the partial segment only the first n_ok of them are rows
+  #define COOT_DIMS_USE(TT, k, row, yv, n_ok)                                                                   \
+    if constexpr (TT < COOT_NT) {                                                                               \
+      typedef coot_tree_flags<TT> F;                                                                            \
+      if (n_ok >= COOT_VEC) {                                                                                   \
+        if constexpr (TT == 0) acc0.add_vec<COOT_VEC, F::SKIP>(yv);                                              \
+        else if constexpr (TT == 1) acc1.add_vec<COOT_VEC, F::SKIP>(yv);                                         \
+        else if constexpr (TT == 2) acc2.add_vec<COOT_VEC, F::SKIP>(yv);                                         \
+        else acc3.add_vec<COOT_VEC, F::SKIP>(yv);                                                                \
+        if constexpr (F::ST) {                                                                                  \
+          typedef typename coot_st<F::TO>::T TOT;                                                               \
+          coot_vstore<F::TO, COOT_VEC>((TOT*)dp.out[TT] + (j * dp.ld_out[TT] + (row)), yv);                     \
+        }                                                                                                       \
+      } else {                                                                                                  \
+        _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) {                                                 \
+          if (v < n_ok) {                                                                                       \
+            if constexpr (TT == 0) acc0.add_vec<1, F::SKIP>(yv + v);                                             \
+            else if constexpr (TT == 1) acc1.add_vec<1, F::SKIP>(yv + v);                                        \
+            else if constexpr (TT == 2) acc2.add_vec<1, F::SKIP>(yv + v);                                        \
+            else acc3.add_vec<1, F::SKIP>(yv + v);                                                               \
+            if constexpr (F::ST) {                                                                              \
+              typedef typename coot_st<F::TO>::T TOT;                                                           \
+              coot_sstore<F::TO>((TOT*)dp.out[TT] + (j * dp.ld_out[TT] + (row) + v), yv[v]);                    \
+            }                                                                                                   \
+          } else {                                                                                              \
+            yv[v] = (COOT_REAL)0; /* adds nothing to the row and column pairs */                                \
+          }                                                                                                     \
+        }                                                                                                       \
+      }                                                                                                         \
+      if constexpr (F::RS) {                                                                                    \
+        _Pragma("unroll") for (int q = 0; q < COOT_RV; ++q)                                                    \
+          coot_racc_add(rsum[coot_rs_slot<TT>::K][k][q], rcmp[coot_rs_slot<TT>::K][k][q], yv + q * COOT_RSTEP);  \
+      }                                                                                                         \
+      if constexpr (F::CS) {                                                                                    \
+        _Pragma("unroll") for (int q = 0; q < COOT_RV; ++q)                                                    \
+          coot_racc_add(csum[coot_cs_slot<TT>::K], ccmp[coot_cs_slot<TT>::K], yv + q * COOT_RSTEP);             \
+      }                                                                                                         \
     }
+  #pragma unroll
+        for (int k = 0; k < COOT_UNROLL; ++k) {
+          COOT_REAL y[4][COOT_VEC];
+          coot_multi_f(xc[k], y);
+          const coot_i64 row = rb + ((coot_i64)k * 32 + lane) * COOT_VEC;
+          const coot_i64 left = p.n_rows - row;
+          const int n_ok = whole ? COOT_VEC : (int)(left < 0 ? 0 : (left > COOT_VEC ? COOT_VEC : left));
+          COOT_DIMS_USE(0, k, row, y[0], n_ok)
+          COOT_DIMS_USE(1, k, row, y[1], n_ok)
+          COOT_DIMS_USE(2, k, row, y[2], n_ok)
+          COOT_DIMS_USE(3, k, row, y[3], n_ok)
+        }
+  #undef COOT_DIMS_USE
+  #if COOT_NCS > 0
+        // the lane's column pair into the batch table
+  #pragma unroll
+        for (int t = 0; t < COOT_NCS; ++t) {
+          // the accumulator's lanes merged (TwoSum of the sums, the error
+          // and the compensations added) into one table entry
+          COOT_REAL en[COOT_ENT];
+          coot_racc_entry(csum[t], ccmp[t], en);
+          COOT_REAL* dst = mine + t * COOT_CTAB + (nb * 33 + lane) * COOT_ENT;
+#pragma unroll
+          for (int w = 0; w < COOT_ENT; ++w) dst[w] = en[w];
+        }
+        if (++nb == COOT_CB) flush();
+  #endif
+    };
+#if COOT_PREFETCH
+    // two register buffers: column j + warps loads while column j computes
+    coot_i64 j = jb + warp;
+    if (j < je) load_col(j, xa);
+    while (j < je) {
+      if (j + COOT_WARPS < je) load_col(j + COOT_WARPS, xb);
+      process(j, xa);
+      j += COOT_WARPS;
+      if (j >= je) break;
+      if (j + COOT_WARPS < je) load_col(j + COOT_WARPS, xa);
+      process(j, xb);
+      j += COOT_WARPS;
+    }
+#else
+    for (coot_i64 j = jb + warp; j < je; j += COOT_WARPS) {
+      load_col(j, xa);
+      process(j, xa);
+    }
+#endif
+#if COOT_NCS > 0
+    if (nb > 0) flush();
+    if (n_seg > 1) {
+      // one fence for the warp's partials of this unit, then an arrival per
+      // column; the last lane to arrive at a column adds its partials in
+      // segment order (lane L takes the warp's columns L, L + 32, ...)
+      __threadfence();
+      __syncwarp();
+      const coot_i64 n_mine = je > jb + warp ? (je - jb - warp + COOT_WARPS - 1) / COOT_WARPS : 0;
+      for (coot_i64 i = lane; i < n_mine; i += 32) {
+        const coot_i64 j = jb + warp + i * COOT_WARPS;
+        if (atomicAdd(cnt_col + j, 1u) == (coot_u32)(n_seg - 1)) {
+          __threadfence();
+          COOT_REAL sh[COOT_NCS1], sl[COOT_NCS1];
+#pragma unroll
+          for (int t = 0; t < COOT_NCS; ++t) {
+            sh[t] = sl[t] = (COOT_REAL)0;
+            for (coot_i64 q = 0; q < n_seg; ++q)
+              coot_dw_add(sh[t], sl[t], __ldcg(cph + 2 * t * cper + j * n_seg + q),
+                          __ldcg(cph + (2 * t + 1) * cper + j * n_seg + q));
+          }
+#define COOT_CS_STORE(TT, h, l)                                                                               \
+  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::CS) {                                                   \
+    typedef typename coot_st<coot_tree_flags<TT>::TCS>::T TCT;                                                \
+    ((TCT*)dp.cs[TT])[j * dp.ld_cs[TT]] =                                                                     \
+        coot_dw_store<coot_tree_flags<TT>::TCS>(h[coot_cs_slot<TT>::K], l[coot_cs_slot<TT>::K]);             \
+  }
+          COOT_CS_STORE(0, sh, sl)
+          COOT_CS_STORE(1, sh, sl)
+          COOT_CS_STORE(2, sh, sl)
+          COOT_CS_STORE(3, sh, sl)
+#undef COOT_CS_STORE
+          cnt_col[j] = 0u;  // ready for the next call
+        }
+      }
+    }
+#endif
 #if COOT_NRS > 0
     // rows of the segment over the chunk: the warps' pairs added in warp
     // order, one summed tree at a time
     COOT_REAL* rph = (COOT_REAL*)(p.ws + dp.rpart);
     const coot_i64 rper = n_chunk * p.n_rows;
-#define COOT_RS_TREE(TT)                                                                                       \
-  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::RS) {                                                     \
-    constexpr int K = coot_rs_slot<TT>::K;                                                                     \
-    typedef typename coot_st<coot_tree_flags<TT>::TRS>::T TRT;                                                 \
+    __syncwarp();  // this warp's column tables are no longer read
+#define COOT_RS_TREE(TT)                                                                                      \
+  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::RS) {                                                   \
+    constexpr int K = coot_rs_slot<TT>::K;                                                                    \
+    typedef typename coot_st<coot_tree_flags<TT>::TRS>::T TRT;                                                \
     _Pragma("unroll") for (int k = 0; k < COOT_UNROLL; ++k)                                                  \
-      _Pragma("unroll") for (int v = 0; v < COOT_VEC; ++v) {                                                 \
-        const int r = (k * 32 + lane) * COOT_VEC + v;                                                         \
-        coot_dw_norm(rsum[K][k][v], rcmp[K][k][v], red_h[warp][r], red_l[warp][r]);                          \
+      _Pragma("unroll") for (int q = 0; q < COOT_RV; ++q) {                                                  \
+        COOT_REAL h[COOT_RSTEP], l[COOT_RSTEP];                                                               \
+        coot_racc_pairs(rsum[K][k][q], rcmp[K][k][q], h, l);                                                  \
+        _Pragma("unroll") for (int w = 0; w < COOT_RSTEP; ++w) {                                             \
+          const int r = (k * 32 + lane) * COOT_VEC + q * COOT_RSTEP + w;                                      \
+          mine[r] = h[w];                                                                                     \
+          mine[COOT_SEG + r] = l[w];                                                                          \
+          if constexpr (coot_tree_flags<TT>::SUM_ROWS) COOT_ADD_PAIR(TT, h[w], l[w])                          \
+        }                                                                                                     \
       }                                                                                                       \
     __syncthreads();                                                                                          \
     for (int r = threadIdx.x; r < COOT_SEG; r += COOT_BLOCK) {                                               \
-      COOT_REAL h = red_h[0][r], l = red_l[0][r];                                                             \
-      _Pragma("unroll") for (int w = 1; w < COOT_WARPS; ++w) coot_dw_add(h, l, red_h[w][r], red_l[w][r]);   \
+      COOT_REAL h = wsm[0][r], l = wsm[0][COOT_SEG + r];                                                      \
+      _Pragma("unroll") for (int w = 1; w < COOT_WARPS; ++w) coot_dw_add(h, l, wsm[w][r], wsm[w][COOT_SEG + r]); \
       const coot_i64 row = rb + r;                                                                            \
       if (row < p.n_rows) {                                                                                   \
         if (n_chunk == 1) {                                                                                   \
-          ((TRT*)dp.rs[TT])[row] = coot_dw_store<coot_tree_flags<TT>::TRS>(h, l);                               \
+          ((TRT*)dp.rs[TT])[row] = coot_dw_store<coot_tree_flags<TT>::TRS>(h, l);                             \
         } else {                                                                                              \
           rph[2 * K * rper + chunk * p.n_rows + row] = h;                                                     \
           rph[(2 * K + 1) * rper + chunk * p.n_rows + row] = l;                                               \
@@ -318,10 +505,10 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
       if (is_last) {
         __threadfence();
         // the segment's rows: the chunk partials in chunk order
-#define COOT_RS_LAST(TT)                                                                                       \
-  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::RS) {                                                     \
-    constexpr int K = coot_rs_slot<TT>::K;                                                                     \
-    typedef typename coot_st<coot_tree_flags<TT>::TRS>::T TRT;                                                 \
+#define COOT_RS_LAST(TT)                                                                                      \
+  if constexpr (TT < COOT_NT && coot_tree_flags<TT>::RS) {                                                   \
+    constexpr int K = coot_rs_slot<TT>::K;                                                                    \
+    typedef typename coot_st<coot_tree_flags<TT>::TRS>::T TRT;                                                \
     for (int r = threadIdx.x; r < COOT_SEG; r += COOT_BLOCK) {                                               \
       const coot_i64 row = rb + r;                                                                            \
       if (row < p.n_rows) {                                                                                   \
@@ -329,7 +516,7 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
         _Pragma("unroll 4") for (coot_i64 c = 0; c < n_chunk; ++c)                                            \
           coot_dw_add(h, l, __ldcg(rph + 2 * K * rper + c * p.n_rows + row),                                 \
                       __ldcg(rph + (2 * K + 1) * rper + c * p.n_rows + row));                                 \
-        ((TRT*)dp.rs[TT])[row] = coot_dw_store<coot_tree_flags<TT>::TRS>(h, l);                                 \
+        ((TRT*)dp.rs[TT])[row] = coot_dw_store<coot_tree_flags<TT>::TRS>(h, l);                               \
       }                                                                                                       \
     }                                                                                                         \
   }
@@ -342,6 +529,8 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
       }
       __syncthreads();  // is_last is rewritten by the next unit
     }
+#else
+    __syncwarp();  // this warp's column tables are rewritten by the next unit
 #endif
   }
 #if COOT_MULTI_NH_ALL > 0
@@ -358,4 +547,5 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK, COOT_MINB) COOT_ENTRY(c
   }
 #endif
 }
+#undef COOT_ADD_PAIR
 #endif

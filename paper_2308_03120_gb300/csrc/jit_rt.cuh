@@ -557,6 +557,21 @@ __device__ __forceinline__ float coot_pairwise2(const float* y, int what) {
 // all / any: 1 for a nonzero value (NaN included), else 0
 __device__ __forceinline__ COOT_REAL coot_nonzero(COOT_REAL y) { return y != (COOT_REAL)0 ? (COOT_REAL)1 : (COOT_REAL)0; }
 
+// The extremum of V values (W = 0: min, 1: max, 2: min of magnitudes,
+// 3: max of magnitudes, 4: min of nonzero indicators, 5: max of them), as
+// a tree of depth log2 V.
+template <int V, int W>
+__device__ __forceinline__ COOT_REAL coot_tree_ext(const COOT_REAL* y) {
+  COOT_REAL t[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) t[v] = (W == 2 || W == 3) ? coot_abs(y[v]) : (W >= 4 ? coot_nonzero(y[v]) : y[v]);
+#pragma unroll
+  for (int w = 1; w < V; w *= 2)
+#pragma unroll
+    for (int v = 0; v + w < V; v += 2 * w) t[v] = (W % 2 == 0) ? coot_min(t[v], t[v + w]) : coot_max(t[v], t[v + w]);
+  return t[0];
+}
+
 // Per-thread accumulators of the reduction heads in the mask H
 // (COOT_HEAD_* bits).
 template <unsigned H>
@@ -597,8 +612,11 @@ struct coot_acc_h {
   // of depth log2 V) and the result enters the running pair with one
   // TwoSum, which keeps 2-byte inputs memory-bound.  Extrema are taken
   // element by element.
-  template <int V>
+  // (SKIP: heads whose values this call leaves out, e.g. a plain sum that
+  // the caller feeds from already-summed pairs with add_pair)
+  template <int V, unsigned SKIP = 0u>
   __device__ __forceinline__ void add_vec(const COOT_REAL* y) {
+    constexpr unsigned HH = H & ~SKIP;
 #if !COOT_REAL_F64
     constexpr bool packed = V % 2 == 0;
 #else
@@ -606,26 +624,37 @@ struct coot_acc_h {
 #endif
     if constexpr (packed) {
 #if !COOT_REAL_F64
-      if constexpr ((H & COOT_HEAD_SUM) != 0) {
+      if constexpr ((HH & COOT_HEAD_SUM) != 0) {
 #pragma unroll
         for (int v = 0; v < V / 2; ++v) coot_two_sum2(s2, sc2, coot_pack(y[2 * v], y[2 * v + 1]));
       }
-      if constexpr ((H & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
-      if constexpr ((H & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
+      if constexpr ((HH & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
+      if constexpr ((HH & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
 #endif
     } else {
-      if constexpr ((H & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
-      if constexpr ((H & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
+      if constexpr ((HH & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
+      if constexpr ((HH & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise<V>(y, 2));
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr ((H & COOT_HEAD_SUM) != 0 && !packed) coot_two_sum(s, sc, y[v]);
-      if constexpr ((H & COOT_HEAD_MIN) != 0) mn = coot_min(mn, y[v]);
-      if constexpr ((H & COOT_HEAD_MAX) != 0) mx = coot_max(mx, y[v]);
-      if constexpr ((H & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_abs(y[v]));
-      if constexpr ((H & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_abs(y[v]));
-      if constexpr ((H & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_nonzero(y[v]));
-      if constexpr ((H & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_nonzero(y[v]));
+      if constexpr ((HH & COOT_HEAD_SUM) != 0 && !packed) coot_two_sum(s, sc, y[v]);
+    }
+    // extrema: the V values in a tree of depth log2 V first, then one step
+    // of the running value (exact in any order; NaN propagates either way),
+    // so the running chain grows by one instruction per vector
+    if constexpr ((HH & COOT_HEAD_MIN) != 0) mn = coot_min(mn, coot_tree_ext<V, 0>(y));
+    if constexpr ((HH & COOT_HEAD_MAX) != 0) mx = coot_max(mx, coot_tree_ext<V, 1>(y));
+    if constexpr ((HH & COOT_HEAD_MINABS) != 0) mna = coot_min(mna, coot_tree_ext<V, 2>(y));
+    if constexpr ((HH & COOT_HEAD_MAXABS) != 0) mxa = coot_max(mxa, coot_tree_ext<V, 3>(y));
+    if constexpr ((HH & COOT_HEAD_ALL) != 0) alz = coot_min(alz, coot_tree_ext<V, 4>(y));
+    if constexpr ((HH & COOT_HEAD_ANY) != 0) anz = coot_max(anz, coot_tree_ext<V, 5>(y));
+  }
+  // the plain sum's share of a normalised double-word partial sum (h, l):
+  // h enters the running pair with TwoSum, l its compensation
+  __device__ __forceinline__ void add_pair(COOT_REAL h, COOT_REAL l) {
+    if constexpr ((H & COOT_HEAD_SUM) != 0) {
+      coot_two_sum(s, sc, h);
+      sc += l;
     }
   }
   // per-head values as FP64, in head-bit order
