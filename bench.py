@@ -30,6 +30,7 @@ import argparse
 import csv
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -217,26 +218,135 @@ class Clocks:
 
 # ---------------------------------------------------------------- oracle (CPU) legs
 
+def sample_inputs(seed, cols):
+    """The first `cols` columns of the matrix workload's A, B, C, D (host)."""
+    return [synth.uniform_f32(seed + k, N * cols, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0) for k in range(4)]
+
+
 def oracle_sample(seed, cols, time_budget=None):
     """Run the oracle over the first `cols` columns of the workload; returns
-    (seconds, algorithmic bytes of the sample)."""
+    (seconds, algorithmic bytes of the sample, the oracle's results)."""
     from oracle import coot_oracle as O
-    A = [synth.as_mat(synth.uniform_f32(seed + k, N * cols, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
-                      "f32", N, cols) for k in range(4)]
+    A = [synth.as_mat(a, "f32", N, cols) for a in sample_inputs(seed, cols)]
     t_expr = O.encode(synth.MAT_EXPR)
     t_chain = O.encode(synth.MAT_CHAIN)
     t0 = time.perf_counter()
     out = O.evaluate(t_expr, A)
-    O.accu(t_expr, A)
-    O.norm(t_expr, A, "fro")
-    O.minmax(t_expr, A)
-    O.evaluate(t_chain, A)
+    accu = O.accu(t_expr, A)
+    norm2 = O.norm(t_expr, A, "fro")
+    lo, hi = O.minmax(t_expr, A)
+    chain = O.evaluate(t_chain, A)
     om = synth.as_mat(out.astype(np.float32).ravel(order="F"), "f32", N, cols)
     leaf = O.encode(synth.LEAF0)
-    O.sum_dim(leaf, [om], 0)
-    O.sum_dim(leaf, [om], 1)
+    col = O.sum_dim(leaf, [om], 0)
+    row = O.sum_dim(leaf, [om], 1)
     dt = time.perf_counter() - t0
-    return dt, sum(STREAMS.values()) * N * cols * ELEM
+    res = {"out": out, "accu": accu, "norm2": norm2, "min": lo, "max": hi, "chain": chain, "col": col, "row": row}
+    return dt, sum(STREAMS.values()) * N * cols * ELEM, res
+
+
+def cpu_fp32_sample(seed, cols, reps=3):
+    """The step on the first `cols` columns by the all-cores FP32 CPU
+    evaluator (oracle/cpu_fp32.c, OpenMP): the matrix tree stored with its
+    accu, sum of squares, min, max and column and row sums in one pass, then
+    the chain tree stored.  Returns (best seconds of `reps`, algorithmic
+    bytes of the sample, threads)."""
+    import ctypes
+    from oracle import cpu_build
+    lib = cpu_build.load()
+    ins = sample_inputs(seed, cols)
+    ptrs = (ctypes.c_void_p * 4)(*[a.ctypes.data for a in ins])
+    t_expr = bytes(coot_tree_bytes(synth.MAT_EXPR))
+    t_chain = bytes(coot_tree_bytes(synth.MAT_CHAIN))
+    out1 = np.empty(N * cols, np.float32)
+    out2 = np.empty(N * cols, np.float32)
+    heads = np.zeros(4)
+    col = np.empty(cols, np.float32)
+    row = np.empty(N, np.float32)
+    best = math.inf
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        rc = lib.cpu_fp32_eval(t_expr, len(t_expr), ptrs, 4, N, cols, N, out1.ctypes.data, N, heads.ctypes.data,
+                               col.ctypes.data, row.ctypes.data, 0)
+        rc |= lib.cpu_fp32_eval(t_chain, len(t_chain), ptrs, 4, N, cols, N, out2.ctypes.data, N, None, None, None, 0)
+        best = min(best, time.perf_counter() - t0)
+        if rc != 0:
+            raise RuntimeError(f"cpu_fp32_eval failed ({rc})")
+    return best, sum(STREAMS.values()) * N * cols * ELEM, lib.cpu_fp32_threads()
+
+
+def coot_tree_bytes(sexpr):
+    """The serialised tree of a workload expression (the oracle's encoder:
+    the CPU legs do not load the CUDA library)."""
+    from oracle import coot_oracle as O
+    return O.encode(sexpr)
+
+
+def matrix_errors(coot, torch, dev, cols):
+    """The step's results on the first `cols` columns of the device inputs,
+    by the four calls of the timed step and by the one-launch call, against
+    the FP64 oracle on the same columns: relative errors of accu and norm2,
+    absolute errors of min / max, the largest relative error of each sum
+    along a dimension, and for the stored trees the largest relative error
+    and the largest error over the element-wise tolerance 1e-5 |o| + 2 E
+    (E the oracle's first-order FP32 error bound of that element)."""
+    from oracle import coot_oracle as O
+    seed = synth.BASE_SEED + 1
+    _, _, want = oracle_sample(seed, cols)
+    host = [synth.as_mat(a, "f32", N, cols) for a in sample_inputs(seed, cols)]
+    mats = [coot.Mat(t, N, cols, N) for t in dev]
+    t_expr, t_chain = coot.serialize(synth.MAT_EXPR), coot.serialize(synth.MAT_CHAIN)
+    leaf = coot.serialize(synth.LEAF0)
+    heads = coot.HEAD_SUM | coot.HEAD_NORM2 | coot.HEAD_MIN | coot.HEAD_MAX
+    ws = coot.Workspace(N)
+    bounds = {}
+    for name, tree in (("expr", t_expr), ("chain", t_chain)):
+        _, e, unsafe = O.error_bound(O.decode(tree), host)
+        bounds[name] = (e, int(unsafe.sum()))
+
+    def elementwise(got, name, ref):
+        g = got.view(cols, N).T.cpu().numpy().astype(np.float64)
+        err = np.abs(g - ref)
+        e, skipped = bounds[name]
+        tol = 1e-5 * np.abs(ref) + 2.0 * e
+        return {"max_rel": float(f"{np.max(err / np.maximum(np.abs(ref), 1e-300)):.3e}"),
+                "max_err_over_tol": float(f"{np.max(err / tol):.3e}"), "unsafe_skipped": skipped}
+
+    def sums(col, row):
+        c = col.cpu().numpy().astype(np.float64)
+        r = row.cpu().numpy().astype(np.float64)
+        return ({"max_rel": float(f"{np.max(np.abs(c - want['col']) / np.abs(want['col'])):.3e}")},
+                {"max_rel": float(f"{np.max(np.abs(r - want['row']) / np.abs(want['row'])):.3e}")})
+
+    def heads_err(res):
+        a, n2, lo, hi = res.cpu().tolist()
+        return {"accu": _rel(a, want["accu"]), "norm2": _rel(n2, want["norm2"]),
+                "min_abs": float(f"{abs(lo - want['min']):.3e}"), "max_abs": float(f"{abs(hi - want['max']):.3e}")}
+
+    o1 = torch.empty(N * cols, device="cuda")
+    o2 = torch.empty(N * cols, device="cuda")
+    col = torch.empty(cols, device="cuda")
+    row = torch.empty(N, device="cuda")
+    O1 = coot.Mat(o1, N, cols, N)
+    res = coot.coot_expr_reduce(t_expr, mats, heads, out=O1, ws=ws)
+    coot.coot_expr_eval(t_chain, mats, coot.Mat(o2, N, cols, N), ws=ws)
+    coot.coot_sum_dim(leaf, [O1], 0, coot.Mat(col, 1, cols, 1), ws=ws)
+    coot.coot_sum_dim(leaf, [O1], 1, coot.Mat(row, N, 1, N), ws=ws)
+    torch.cuda.synchronize()
+    four = dict(heads_err(res), expr_eval=elementwise(o1, "expr", want["out"]),
+                chain=elementwise(o2, "chain", want["chain"]))
+    four["sum_dim0"], four["sum_dim1"] = sums(col, row)
+    o1.fill_(float("nan"))
+    o2.fill_(float("nan"))
+    res = coot.coot_expr_multi_dims([t_expr, t_chain], mats, [O1, coot.Mat(o2, N, cols, N)],
+                                    [heads | coot.HEAD_COLSUM | coot.HEAD_ROWSUM, 0],
+                                    [coot.Mat(col, 1, cols, 1), None], [coot.Mat(row, N, 1, N), None], ws=ws)
+    torch.cuda.synchronize()
+    one = dict(heads_err(res), expr_eval=elementwise(o1, "expr", want["out"]),
+               chain=elementwise(o2, "chain", want["chain"]))
+    one["sum_dim0"], one["sum_dim1"] = sums(col, row)
+    return {"vs": "FP64 oracle", "sample": f"the step's calls on the first {cols} of {N} columns",
+            "four_calls": four, "one_launch": one}
 
 
 def run_reference(args):
@@ -250,7 +360,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_sample(seed, cols)
     for _ in range(args.steps):
-        dt, nbytes = oracle_sample(seed, cols)
+        dt, nbytes, _ = oracle_sample(seed, cols)
         times.append(dt)
     ms = 1e3 * statistics.mean(times)
     gbs = nbytes / (statistics.mean(times) * 1e9)
@@ -576,9 +686,25 @@ def run_coot(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, nbytes = oracle_sample(seed, args.cpu_cols)
+        dt, nbytes, _ = oracle_sample(seed, args.cpu_cols)
         cpu = {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{N} x {args.cpu_cols} column block of every matrix, whole step, {dt:.1f} s"}
+        dt_all, nbytes_all, threads = cpu_fp32_sample(seed, args.cpu_cols)
+        cpu["all_cores"] = {"value": round(nbytes_all / dt_all / 1e9, 3), "unit": "GB/s", "cores": threads,
+                            "os_cpu_count": os.cpu_count(), "kind": "fp32 OpenMP evaluator (oracle/cpu_fp32.c)",
+                            "sample": f"{N} x {args.cpu_cols} column block of every matrix, whole step, best of 3, "
+                                      f"{dt_all * 1e3:.1f} ms"}
+    errors = None
+    if rank == 0 and not args.no_errors:
+        errors = matrix_errors(coot, torch, dev, args.err_cols)
+    workloads = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        # the other workloads, each with its own timing and clock record
+        # (supplementary: `value` is the matrix step above)
+        workloads = {"vectors": vectors_result(args),
+                     "precision_bf16": precision_result(args, "bf16", error_elems=1 << 24),
+                     "precision_f16": precision_result(args, "f16", error_elems=1 << 24),
+                     "batched": batched_result(args)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -611,6 +737,8 @@ def run_coot(args):
                          "traffic": traffic, "traffic_note": traffic_note, "launch": shapes[dom],
                          "algorithmic_bytes": STREAMS[dom] * MAT_BYTES},
             "cpu_baseline": cpu,
+            "errors": errors,
+            "workloads": workloads,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
@@ -621,6 +749,13 @@ def run_coot(args):
 
 
 # ---------------------------------------------------------------- other workloads (one JSON line each)
+
+def _rel(got, want):
+    """|got - want| / |want| in three significant digits (the absolute
+    difference when want is 0)."""
+    d = abs(got - want) / abs(want) if want != 0 else abs(got - want)
+    return float(f"{d:.3e}")
+
 
 def _timed(torch, stream, fn, steps, warmup):
     """Device time of `fn` per call (CUDA events on `stream`)."""
@@ -650,19 +785,22 @@ def _graph(torch, fn):
     return g
 
 
-def run_vectors(args):
+def vectors_result(args):
     """FP32 vectors n = 1,000,000: y = 2x + 3z, accu(x % z), norm2(x).  The
     step is latency-bound (24 MB fits in L2): reported as microseconds per
-    step, eager calls and as one CUDA graph."""
+    step, eager calls and as one CUDA graph; plus the errors of accu(x % z)
+    and norm2(x) against the FP64 oracle."""
     import torch
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build as _build
+    from oracle import coot_oracle as O
     _build.build()
     coot.coot_init(0)
     n = 1_000_000
     seed = synth.BASE_SEED
-    x = torch.from_numpy(synth.uniform_f32(seed, n)).cuda()
-    z = torch.from_numpy(synth.uniform_f32(seed + 1, n)).cuda()
+    hx, hz = synth.uniform_f32(seed, n), synth.uniform_f32(seed + 1, n)
+    x = torch.from_numpy(hx).cuda()
+    z = torch.from_numpy(hz).cuda()
     y = torch.empty(n, device="cuda")
     X, Z, Y = coot.Mat(x, n, 1, n), coot.Mat(z, n, 1, n), coot.Mat(y, n, 1, n)
     res = torch.empty(2, dtype=torch.float64, device="cuda")
@@ -684,26 +822,79 @@ def run_vectors(args):
         coot.coot_expr_multi(trees, [X, Z], [Y, None, None], heads, out_dev=res, ws=ws, stream=s)
 
     stream = torch.cuda.current_stream()
-    ms = _timed(torch, stream, step, args.steps, args.warmup)
     g = _graph(torch, step)
+    gm = _graph(torch, step_multi)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms = _timed(torch, stream, step, args.steps, args.warmup)
     ms_g = _timed(torch, stream, g.replay, args.steps, args.warmup)
     ms_m = _timed(torch, stream, step_multi, args.steps, args.warmup)
-    gm = _graph(torch, step_multi)
     ms_mg = _timed(torch, stream, gm.replay, args.steps, args.warmup)
+    clk = clocks.stop()
+    step()
+    torch.cuda.synchronize()
+    got = res.cpu().tolist()
+    hs = [synth.as_mat(hx, "f32", n, 1), synth.as_mat(hz, "f32", n, 1)]
+    want = [O.accu(t_schur, hs), O.norm(leaf, hs[:1], 2)]
+    yw = O.evaluate(t_axpy, hs).ravel()
+    yg = y.cpu().numpy().astype(np.float64)
     nbytes = (3 + 2 + 1) * n * 4
-    print(json.dumps({"metric": "fused vector step latency", "workload": "vectors n=1e6 fp32: 2x+3z, accu(x%z), "
-                      "norm2(x)", "us_per_step": round(ms * 1e3, 2), "us_per_step_graph": round(ms_g * 1e3, 2),
-                      "gbs_graph": round(nbytes / (ms_g * 1e-3) / 1e9, 1), "bytes_per_step": nbytes,
-                      "launches_per_step": 3,
-                      "one_pass": {"us_per_step": round(ms_m * 1e3, 2), "us_per_step_graph": round(ms_mg * 1e3, 2),
-                                   "launches_per_step": 1, "bytes_per_step": 3 * n * 4,
-                                   "call": "coot_expr_multi: 2x+3z stored, accu(x%z), norm2(x)"},
-                      "note": "24 MB per step is L2-resident: latency, not HBM, bound"}))
+    return {"metric": "fused vector step latency", "workload": "vectors n=1e6 fp32: 2x+3z, accu(x%z), norm2(x)",
+            "us_per_step": round(ms * 1e3, 2), "us_per_step_graph": round(ms_g * 1e3, 2),
+            "gbs_graph": round(nbytes / (ms_g * 1e-3) / 1e9, 1), "bytes_per_step": nbytes,
+            "launches_per_step": 3,
+            "one_pass": {"us_per_step": round(ms_m * 1e3, 2), "us_per_step_graph": round(ms_mg * 1e3, 2),
+                         "launches_per_step": 1, "bytes_per_step": 3 * n * 4,
+                         "call": "coot_expr_multi: 2x+3z stored, accu(x%z), norm2(x)"},
+            "errors": {"vs": "FP64 oracle", "accu(x%z)": _rel(got[0], want[0]), "norm2(x)": _rel(got[1], want[1]),
+                       "2x+3z max_rel": float(f"{np.max(np.abs(yg - yw) / np.maximum(np.abs(yw), 1e-300)):.3e}")},
+            "note": "24 MB per step is L2-resident: latency, not HBM, bound", "clocks": clk}
 
 
-def run_precision(args, dt):
+def run_vectors(args):
+    print(json.dumps(vectors_result(args)), flush=True)
+
+
+def precision_errors(dt, hx, hz, y_bits, got, n):
+    """Errors of the precision workload's results over the first n elements
+    against the FP64 oracle: relative errors of accu(x), norm2(x) and
+    dot(x, z) (exact oracle sums), and for y = 2x + 3z stored in dt the
+    largest distance in storage ulps from the oracle value rounded to dt and
+    the fraction of elements equal to it."""
+    from oracle import coot_oracle as O
+    step = 1 << 24
+    chunks = range(0, n, step)
+    vx = lambda i: O.decode_storage(hx[i:min(i + step, n)], dt)  # noqa: E731
+    vz = lambda i: O.decode_storage(hz[i:min(i + step, n)], dt)  # noqa: E731
+    acc = O._fsum(vx(i) for i in chunks)
+    nrm = math.sqrt(O._fsum(vx(i) ** 2 for i in chunks))
+    dot = O._fsum(vx(i) * vz(i) for i in chunks)
+    tree = O.encode(synth.AXPY_2X_3Z)
+    p, emin, _ = O.FORMATS[dt]
+    worst, exact = 0.0, 0
+    for i in chunks:
+        m = min(i + step, n) - i
+        ins = [synth.as_mat(hx[i:i + m], dt, m, 1), synth.as_mat(hz[i:i + m], dt, m, 1)]
+        ref = O.round_to_format(O.evaluate(tree, ins).ravel(), dt)
+        g = O.decode_storage(y_bits[i:i + m], dt)
+        fin = np.isfinite(ref)
+        a = np.abs(ref[fin])
+        _, ex = np.frexp(np.where(a > 0, a, 1.0))
+        ulp = np.ldexp(1.0, np.maximum(ex - 1, emin) - (p - 1))
+        d = np.abs(g[fin] - ref[fin]) / ulp
+        worst = max(worst, float(d.max()) if d.size else 0.0)
+        exact += int(np.sum(d == 0)) + int(np.sum(~fin & (g == ref)))
+    return {"vs": "FP64 oracle", "elements": n, "accu(x)": _rel(got[0], acc), "norm2(x)": _rel(got[1], nrm),
+            "dot(x,z)": _rel(got[2], dot),
+            f"2x+3z max {dt} ulps": worst, "2x+3z exact_frac": round(exact / n, 6)}
+
+
+def precision_result(args, dt, error_elems=None):
     """n = 2^28 stored as BF16 or FP16 (signed lognormal, sigma 2): y = 2x + 3z
-    stored in the same type, accu(x) and norm2(x) in one pass, dot(x, z)."""
+    stored in the same type, accu(x) and norm2(x) in one pass, dot(x, z);
+    the errors of every result against the FP64 oracle over all 2^28
+    elements, or, with error_elems, over the calls' results on the first
+    error_elems elements."""
     import torch
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build as _build
@@ -712,8 +903,8 @@ def run_precision(args, dt):
     n = 1 << 28
     seed = synth.BASE_SEED + 2
     tdt = torch.bfloat16 if dt == "bf16" else torch.float16
-    hx, _ = synth.lognormal_signed(seed, n, dt)
-    hz, _ = synth.lognormal_signed(seed + 1, n, dt)
+    hx, rx = synth.lognormal_signed(seed, n, dt)
+    hz, rz = synth.lognormal_signed(seed + 1, n, dt)
 
     def dev(h):
         t = torch.from_numpy(h.view(np.int16)).view(tdt) if dt == "bf16" else torch.from_numpy(h)
@@ -736,19 +927,40 @@ def run_precision(args, dt):
     out = {}
     total_ms = 0.0
     total_b = 0
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     for name, (fn, nbytes) in calls.items():
         ms = _timed(torch, stream, fn, args.steps, args.warmup)
         out[name] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
-                     "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+                     "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                     "launch": shape_text(coot.coot_last_launch())}
         total_ms += ms
         total_b += nbytes
-    print(json.dumps({"metric": "fused low-precision step HBM GB/s", "workload": f"vectors n=2^28 {dt}",
-                      "value": round(total_b / (total_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
-                      "frac_of_hbm_peak": round(total_b / (total_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": kind,
-                      "calls": out}))
+    clk = clocks.stop()
+    # the errors: the same calls over all n elements, or over a prefix
+    m = n if error_elems is None else min(n, error_elems)
+    Xm, Zm, Ym = coot.Mat(x, m, 1, m), coot.Mat(z, m, 1, m), coot.Mat(y, m, 1, m)
+    coot.coot_expr_eval(t_axpy, [Xm, Zm], Ym)
+    coot.coot_expr_reduce(leaf, [Xm], coot.HEAD_SUM | coot.HEAD_NORM2, out_dev=res[0:2], ws=ws)
+    coot.coot_dot(Xm, Zm, out_dev=res[2:3], ws=ws)
+    torch.cuda.synchronize()
+    got = res.cpu().tolist()
+    yh = y[:m].cpu()
+    y_bits = yh.view(torch.int16).numpy().view(np.uint16) if dt == "bf16" else yh.numpy()
+    errors = precision_errors(dt, hx, hz, y_bits, got, m)
+    if error_elems is not None:
+        errors["sample"] = f"the three calls on the first {m} of {n} elements"
+    return {"metric": "fused low-precision step HBM GB/s", "workload": f"vectors n=2^28 {dt}",
+            "value": round(total_b / (total_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+            "frac_of_hbm_peak": round(total_b / (total_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": kind,
+            "calls": out, "errors": errors, "fp16_redraws": rx + rz if dt == "f16" else 0, "clocks": clk}
 
 
-def run_batched(args):
+def run_precision(args, dt):
+    print(json.dumps(precision_result(args, dt)), flush=True)
+
+
+def batched_result(args):
     """4096 FP32 matrices, rows and cols log-uniform in [1, 512]:
     out = exp(-abs(A)) % B + 0.5 C and sum(out, 0) per matrix, in one
     persistent launch captured as a CUDA graph, against one launch per
@@ -788,8 +1000,11 @@ def run_batched(args):
         coot.coot_expr_eval_batched(tree, [0, 0, 0], 0, 0, plan, n_items, n_work, stream=s)
 
     g = _graph(torch, batched)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     ms_graph = _timed(torch, stream, g.replay, args.steps, args.warmup)
     ms_eager = _timed(torch, stream, batched, args.steps, args.warmup)
+    clk = clocks.stop()
     ws = coot.Workspace(1)
 
     def per_matrix(s=None):
@@ -806,16 +1021,20 @@ def run_batched(args):
     elems = int(sizes.sum())
     nbytes = elems * 4 * 4 + int(cols.sum()) * 4
     peak, kind = peaks()
-    print(json.dumps({
+    return {
         "metric": "batch evals/s", "workload": "4096 fp32 matrices, rows/cols log-uniform [1,512]: "
         "exp(-abs(A))%B+0.5C and column sums", "unit": "matrices/s",
         "value": round(nmat / (ms_graph * 1e-3), 1), "batches_per_s": round(1.0 / (ms_graph * 1e-3), 1),
         "ms_per_batch_graph": round(ms_graph, 4), "ms_per_batch_eager": round(ms_eager, 4),
         "gbs": round(nbytes / (ms_graph * 1e-3) / 1e9, 1), "frac_of_hbm_peak": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
-        "elements": elems, "work_units": n_work,
+        "peak_kind": kind, "elements": elems, "work_units": n_work,
         "per_matrix_launches": {"ms_eager": round(ms_per, 3), "ms_graph": round(ms_per_graph, 3), "launches": 2 * nmat},
         "speedup_vs_per_matrix_eager": round(ms_per / ms_graph, 1),
-        "speedup_vs_per_matrix_graph": round(ms_per_graph / ms_graph, 1)}))
+        "speedup_vs_per_matrix_graph": round(ms_per_graph / ms_graph, 1), "clocks": clk}
+
+
+def run_batched(args):
+    print(json.dumps(batched_result(args)), flush=True)
 
 
 def run_stats(args):
@@ -994,16 +1213,7 @@ def run_views(args):
     print(json.dumps({"metric": "fused evaluation and sums over submatrix views HBM GB/s", "workload":
                       f"{n}x{n} window at ({w0}, {w0}) of {N}x{N} fp32 matrices (ld {N})", "unit": "GB/s",
                       "calls": calls,
-            "one_pass": {"ms_per_step": round(ms_one, 4), "step_speedup": round(ms_step / ms_one, 3),
-                         "gbs": round(world * one_bytes / (ms_one * 1e-3) / 1e9, 1),
-                         "algorithmic_bytes": one_bytes,
-                         "calls": "coot_expr_multi (both trees, inputs read once) + two coot_sum_dim"},
-            "one_launch": {"ms_per_step": round(ms_launch, 4), "step_speedup": round(ms_step / ms_launch, 3),
-                           "gbs": round(world * launch_bytes / (ms_launch * 1e-3) / 1e9, 1),
-                           "frac": round(launch_bytes / (ms_launch * 1e-3) / 1e9 / peak, 4),
-                           "algorithmic_bytes": launch_bytes, "launch": launch_shape,
-                           "calls": "coot_expr_multi_dims: both trees stored, accu/norm2/min/max, sum dim 0 "
-                                    "and dim 1 of out, one kernel"}, "peak": peak, "peak_kind": peak_kind,
+                      "peak": peak, "peak_kind": peak_kind,
                       "l2": "inputs larger than L2, no flush"}), flush=True)
 
 
@@ -1043,6 +1253,10 @@ def main():
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-per-matrix", action="store_true", help="batched: skip the one-launch-per-matrix leg")
+    ap.add_argument("--no-errors", action="store_true", help="skip the errors against the oracle")
+    ap.add_argument("--err-cols", type=int, default=512, help="columns in the errors' sample")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="matrices: skip the vectors, precision and batched workloads in the same line")
     ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
     ap.add_argument("--workload", default="matrices",
                     choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats", "convert", "canonical", "views"],

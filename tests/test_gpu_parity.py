@@ -439,9 +439,12 @@ def test_unfused_baseline_matches(sexpr):
     check_elementwise(tree, ins[:n_in], out.host())
 
 
-def test_shard_local_results_on_gpu():
+@pytest.mark.parametrize("backend", ["gloo", "nccl"])
+def test_shard_local_results_on_gpu(backend):
     """The per-rank reductions of the sharded path (shard.gpu_local) through
-    the combine, as a one-rank gloo group, against the oracle."""
+    the combine, as a one-rank group, against the oracle: with NCCL the
+    partials and the exchange stay on the GPU (device tensors in and out),
+    with gloo they cross to the host."""
     import os
     import socket
 
@@ -456,9 +459,16 @@ def test_shard_local_results_on_gpu():
         port = s.getsockname()[1]
     os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
     os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=0, world_size=1)
+    if backend == "nccl":
+        dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    else:
+        dist.init_process_group("gloo", rank=0, world_size=1)
     try:
-        res = combine(gpu_local(tree, dev), c)
+        local = gpu_local(tree, dev)
+        assert local.heads.is_cuda and local.row_sums.is_cuda and local.col_sums.is_cuda
+        res = combine(local, c)
+        assert all(t.is_cuda == (backend == "nccl") for t in res.values())
+        res = {k: (v.item() if v.dim() == 0 else v.cpu().numpy()) for k, v in res.items()}
     finally:
         dist.destroy_process_group()
     t, e = _terms(tree, ins)

@@ -262,6 +262,8 @@ def test_column_blocks_merge_to_the_whole():
         blocks = [m.cols(c0, c1 - 1) for m in dev]
         parts.append(shard.gpu_local_stats(tree, blocks))
     merged = shard.merge_stats(parts, r, 0)
+    assert merged["rows"]["sum"].is_cuda        # merged on the device that holds the blocks
+    merged = {part: {k: v.cpu().numpy() for k, v in merged[part].items()} for part in ("rows", "cols")}
     for s in NAMES:
         want_rows = O.stats_dim(tree, ins, 1, s)
         np.testing.assert_allclose(merged["rows"][s], want_rows, rtol=2e-6, atol=1e-6, err_msg=s)

@@ -30,9 +30,9 @@ def _oracle_local(tree, mats, rank, world):
     if n:
         v = O.evaluate(tree, blk)
         lo, hi = O.minmax(tree, blk)
-        return LocalResults(O.accu(tree, blk), O._fsum(v * v), lo, hi, n, O.sum_dim(tree, blk, 0),
-                            O.sum_dim(tree, blk, 1))
-    return LocalResults(0.0, 0.0, math.inf, -math.inf, 0, np.zeros(0), np.zeros(r))
+        return LocalResults.from_values(O.accu(tree, blk), O._fsum(v * v), lo, hi, n, O.sum_dim(tree, blk, 0),
+                                        O.sum_dim(tree, blk, 1))
+    return LocalResults.from_values(0.0, 0.0, math.inf, -math.inf, 0, np.zeros(0), np.zeros(r))
 
 
 def _worker(rank, world, port, shape, seed, nan_at, q):
@@ -50,7 +50,8 @@ def _worker(rank, world, port, shape, seed, nan_at, q):
             mats.append(synth.as_mat(flat, "f32", r, c))
         tree = O.encode(synth.MAT_EXPR)
         res = combine(_oracle_local(tree, mats, rank, world), c)
-        q.put((rank, res))
+        assert all(t.device.type == "cpu" for t in res.values())   # gloo exchanges host tensors
+        q.put((rank, {k: (v.item() if v.dim() == 0 else v.numpy()) for k, v in res.items()}))
     finally:
         dist.destroy_process_group()
 
@@ -116,10 +117,11 @@ def _oracle_local_stats(tree, mats, rank, world, norm_type):
     r, w = mats[0].n_rows, c1 - c0
     blk = [synth.as_mat(m.buf[c0 * m.ld:c1 * m.ld].copy(), m.dtype, r, w, m.ld) for m in mats]
     if w == 0:
-        return LocalStats(0, np.zeros(r), np.zeros(r), np.full(r, np.inf), np.full(r, -np.inf), np.zeros((6, 0)))
+        return LocalStats.from_values(0, np.zeros(r), np.zeros(r), np.full(r, np.inf), np.full(r, -np.inf),
+                                      np.zeros((6, 0)))
     st = lambda dim, s, nt=0: O.stats_dim(tree, blk, dim, s, nt)  # noqa: E731
     cols = np.stack([st(0, s, norm_type) for s in O.STATS])
-    return LocalStats(w, st(1, "sum"), st(1, "var", 1) * w, st(1, "min"), st(1, "max"), cols)
+    return LocalStats.from_values(w, st(1, "sum"), st(1, "var", 1) * w, st(1, "min"), st(1, "max"), cols)
 
 
 def _stats_worker(rank, world, port, shape, seed, norm_type, q):
@@ -133,7 +135,8 @@ def _stats_worker(rank, world, port, shape, seed, norm_type, q):
         mats = [synth.as_mat(synth.uniform_f32(seed + k, r * c, 0.0 if k == 3 else -1.0, 2.0 if k == 3 else 1.0),
                              "f32", r, c) for k in range(4)]
         tree = O.encode(synth.MAT_EXPR)
-        q.put((rank, combine_stats(_oracle_local_stats(tree, mats, rank, world, norm_type), r, c, norm_type)))
+        res = combine_stats(_oracle_local_stats(tree, mats, rank, world, norm_type), r, c, norm_type)
+        q.put((rank, {part: {k: v.numpy() for k, v in res[part].items()} for part in ("rows", "cols")}))
     finally:
         dist.destroy_process_group()
 
