@@ -323,6 +323,19 @@ def matrix_errors(coot, torch, dev, cols):
         return {"accu": _rel(a, want["accu"]), "norm2": _rel(n2, want["norm2"]),
                 "min_abs": float(f"{abs(lo - want['min']):.3e}"), "max_abs": float(f"{abs(hi - want['max']):.3e}")}
 
+    def summation_only(res, stored, col, row):
+        """The sums against the correctly rounded sums (math.fsum) of the very
+        FP32 values the GPU stored: the summation's own error, without the
+        values' FP32 rounding that the oracle comparison includes."""
+        v = stored.view(cols, N).T.cpu().numpy().astype(np.float64)
+        c = col.cpu().numpy().astype(np.float64)
+        r = row.cpu().numpy().astype(np.float64)
+        fc = np.array([math.fsum(v[:, k]) for k in range(cols)])
+        fr = np.array([math.fsum(v[i, :]) for i in range(N)])
+        rel = lambda g, w: float(f"{np.max(np.abs(g - w) / np.maximum(np.abs(w), 1e-300)):.3e}")  # noqa: E731
+        return {"accu": _rel(res.cpu().tolist()[0], math.fsum(v.ravel())), "sum_dim0_max_rel": rel(c, fc),
+                "sum_dim1_max_rel": rel(r, fr)}
+
     o1 = torch.empty(N * cols, device="cuda")
     o2 = torch.empty(N * cols, device="cuda")
     col = torch.empty(cols, device="cuda")
@@ -336,6 +349,7 @@ def matrix_errors(coot, torch, dev, cols):
     four = dict(heads_err(res), expr_eval=elementwise(o1, "expr", want["out"]),
                 chain=elementwise(o2, "chain", want["chain"]))
     four["sum_dim0"], four["sum_dim1"] = sums(col, row)
+    four["summation_only"] = summation_only(res, o1, col, row)
     o1.fill_(float("nan"))
     o2.fill_(float("nan"))
     res = coot.coot_expr_multi_dims([t_expr, t_chain], mats, [O1, coot.Mat(o2, N, cols, N)],
@@ -345,6 +359,7 @@ def matrix_errors(coot, torch, dev, cols):
     one = dict(heads_err(res), expr_eval=elementwise(o1, "expr", want["out"]),
                chain=elementwise(o2, "chain", want["chain"]))
     one["sum_dim0"], one["sum_dim1"] = sums(col, row)
+    one["summation_only"] = summation_only(res, o1, col, row)
     return {"vs": "FP64 oracle", "sample": f"the step's calls on the first {cols} of {N} columns",
             "four_calls": four, "one_launch": one}
 

@@ -12,7 +12,8 @@ extern "C" __global__ void __launch_bounds__(COOT_BLOCK) COOT_ENTRY(const __grid
   coot_acc acc;
   acc.init();
   for (coot_i64 u = blockIdx.x; u < units; u += gridDim.x) {
-    const coot_i64 j = u / upc;
+    // (one column, the dense case: no 64-bit division per unit)
+    const coot_i64 j = p.n_cols == 1 ? 0 : u / upc;
     const coot_i64 r0 = (u - j * upc) * TILE;
     if (r0 + TILE <= p.n_rows) {
       COOT_REAL xv[COOT_UNROLL][4][COOT_VEC];

@@ -520,10 +520,10 @@ __device__ __forceinline__ void coot_two_sum2(coot_f2& s, coot_f2& c, coot_f2 x)
   c = coot_add2(c, e);
 }
 // Pairwise sum of V (even) values, what = 1: their squares (each rounded),
-// 2: their magnitudes; lanes hold the even and odd elements, added in a tree
-// of depth log2(V / 2), then the two lanes.
+// 2: their magnitudes, as one packed pair: lanes hold the even and odd
+// elements, each added in a tree of depth log2(V / 2).
 template <int V>
-__device__ __forceinline__ float coot_pairwise2(const float* y, int what) {
+__device__ __forceinline__ coot_f2 coot_pairwise2(const float* y, int what) {
   coot_f2 t[V / 2];
 #pragma unroll
   for (int v = 0; v < V / 2; ++v) {
@@ -534,9 +534,22 @@ __device__ __forceinline__ float coot_pairwise2(const float* y, int what) {
   for (int w = 1; w < V / 2; w *= 2)
 #pragma unroll
     for (int v = 0; v + w < V / 2; v += 2 * w) t[v] = coot_add2(t[v], t[v + w]);
-  float a, b;
-  coot_unpack(t[0], a, b);
-  return a + b;
+  return t[0];
+}
+#endif
+
+#if !COOT_REAL_F64
+// (h, l) += both lanes of a packed (sum, compensation) pair, each lane an
+// exact pair normalised first
+__device__ __forceinline__ void coot_add_lanes(coot_f2 s2, coot_f2 c2, float& h, float& l) {
+  float sa, sb, ca, cb;
+  coot_unpack(s2, sa, sb);
+  coot_unpack(c2, ca, cb);
+  float ha, la, hb, lb;
+  coot_dw_norm(sa, ca, ha, la);
+  coot_dw_norm(sb, cb, hb, lb);
+  coot_dw_add(h, l, ha, la);
+  coot_dw_add(h, l, hb, lb);
 }
 #endif
 
@@ -583,12 +596,14 @@ struct coot_acc_h {
   COOT_REAL mna, mxa;  // min, max magnitude
   COOT_REAL alz, anz;  // all: smallest nonzero indicator; any: largest
 #if !COOT_REAL_F64
-  coot_f2 s2, sc2;  // the sum of vectors, two lanes (even and odd elements)
+  // packed accumulators, two lanes each (even and odd elements): the sum in
+  // two chains (alternate pairs of a vector), squares and magnitudes in one
+  coot_f2 s2[2], sc2[2], q2, qc2, a2, ac2;
 #endif
 
   __device__ __forceinline__ void init() {
 #if !COOT_REAL_F64
-    s2 = sc2 = 0ull;
+    s2[0] = s2[1] = sc2[0] = sc2[1] = q2 = qc2 = a2 = ac2 = 0ull;
 #endif
     s = sc = q = qc = a = ac = (COOT_REAL)0;
     mn = mna = alz = (COOT_REAL)COOT_INF_F;
@@ -626,10 +641,10 @@ struct coot_acc_h {
 #if !COOT_REAL_F64
       if constexpr ((HH & COOT_HEAD_SUM) != 0) {
 #pragma unroll
-        for (int v = 0; v < V / 2; ++v) coot_two_sum2(s2, sc2, coot_pack(y[2 * v], y[2 * v + 1]));
+        for (int v = 0; v < V / 2; ++v) coot_two_sum2(s2[v & 1], sc2[v & 1], coot_pack(y[2 * v], y[2 * v + 1]));
       }
-      if constexpr ((HH & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise2<V>(y, 1));
-      if constexpr ((HH & COOT_HEAD_SUMABS) != 0) coot_two_sum(a, ac, coot_pairwise2<V>(y, 2));
+      if constexpr ((HH & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum2(q2, qc2, coot_pairwise2<V>(y, 1));
+      if constexpr ((HH & COOT_HEAD_SUMABS) != 0) coot_two_sum2(a2, ac2, coot_pairwise2<V>(y, 2));
 #endif
     } else {
       if constexpr ((HH & (COOT_HEAD_SUMSQ | COOT_HEAD_NORM2)) != 0) coot_two_sum(q, qc, coot_pairwise<V>(y, 1));
@@ -665,21 +680,22 @@ struct coot_acc_h {
     if constexpr ((H & COOT_HEAD_SUM) != 0) {
       coot_dw_norm(s, sc, h[k], l[k]);
 #if !COOT_REAL_F64
-      // the two packed lanes, each an exact (sum, compensation) pair
-      float sa, sb, ca, cb;
-      coot_unpack(s2, sa, sb);
-      coot_unpack(sc2, ca, cb);
-      COOT_REAL ha, la, hb, lb;
-      coot_dw_norm(sa, ca, ha, la);
-      coot_dw_norm(sb, cb, hb, lb);
-      coot_dw_add(h[k], l[k], ha, la);
-      coot_dw_add(h[k], l[k], hb, lb);
+      coot_add_lanes(s2[0], sc2[0], h[k], l[k]);
+      coot_add_lanes(s2[1], sc2[1], h[k], l[k]);
 #endif
       ++k;
     }
-    if constexpr ((H & COOT_HEAD_SUMSQ) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
-    if constexpr ((H & COOT_HEAD_NORM2) != 0) { coot_dw_norm(q, qc, h[k], l[k]); ++k; }
-    if constexpr ((H & COOT_HEAD_SUMABS) != 0) { coot_dw_norm(a, ac, h[k], l[k]); ++k; }
+    // sums of squares and magnitudes: the scalar pair plus the packed lanes
+    COOT_REAL qh, ql, ah, al;
+    coot_dw_norm(q, qc, qh, ql);
+    coot_dw_norm(a, ac, ah, al);
+#if !COOT_REAL_F64
+    coot_add_lanes(q2, qc2, qh, ql);
+    coot_add_lanes(a2, ac2, ah, al);
+#endif
+    if constexpr ((H & COOT_HEAD_SUMSQ) != 0) { h[k] = qh; l[k] = ql; ++k; }
+    if constexpr ((H & COOT_HEAD_NORM2) != 0) { h[k] = qh; l[k] = ql; ++k; }
+    if constexpr ((H & COOT_HEAD_SUMABS) != 0) { h[k] = ah; l[k] = al; ++k; }
     if constexpr ((H & COOT_HEAD_MIN) != 0) { h[k] = mn; l[k] = 0; ++k; }
     if constexpr ((H & COOT_HEAD_MAX) != 0) { h[k] = mx; l[k] = 0; ++k; }
     if constexpr ((H & COOT_HEAD_MINABS) != 0) { h[k] = mna; l[k] = 0; ++k; }
