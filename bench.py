@@ -1234,22 +1234,32 @@ def run_views(args):
 
 def run_learned(args):
     """Learned launch shapes on random trees the model never saw (fresh
-    seed): regret against the exhaustive tuner, model and built-in."""
+    seeds): regret against the exhaustive tuner, model and built-in, over
+    the training range of sizes (2^10 to 2^26 elements) and over larger
+    calls (2^26 to 2^30 elements, never in training)."""
     import paper_2308_03120_gb300 as coot
     from paper_2308_03120_gb300 import build as _build, learn
     _build.build()
     coot.coot_init(0)
     t0 = time.time()
-    samples = learn.generate(args.learned_trees, seed=4242, max_log2=26, log=lambda *a: None)
     learn.load_policy()   # loads the model for host_predict
     learn.use_builtin()
-    r = learn.regret(samples, learn.host_predict)
+    bands = {}
+    for name, n_trees, seed, lo, hi in (("2^10..2^26", args.learned_trees, 4242, 10, 26),
+                                        ("2^26..2^30", args.learned_large_trees, 4343, 26, 30)):
+        if n_trees <= 0:
+            continue
+        samples = learn.generate(n_trees, seed=seed, min_log2=lo, max_log2=hi, log=lambda *a: None)
+        r = learn.regret(samples, learn.host_predict)
+        bands[name] = {"model_geomean": round(r["model_geomean"], 4), "builtin_geomean": round(r["builtin_geomean"], 4),
+                       "model_within_5pct": round(r["model_within_5pct"], 3),
+                       "builtin_within_5pct": round(r["builtin_within_5pct"], 3),
+                       "model_worst": round(r["model_worst"], 3), "samples": r["samples"], "unseen_trees": n_trees,
+                       "seed": seed}
+    first = next(iter(bands.values()))
     print(json.dumps({"metric": "learned launch-shape regret vs exhaustive tuner (geomean, lower is better)",
-                      "value": round(r["model_geomean"], 4), "unit": "ratio", "higher_is_better": False,
-                      "builtin": round(r["builtin_geomean"], 4), "target": 1.05,
-                      "model_within_5pct": round(r["model_within_5pct"], 3),
-                      "builtin_within_5pct": round(r["builtin_within_5pct"], 3),
-                      "samples": r["samples"], "unseen_trees": args.learned_trees,
+                      "value": first["model_geomean"], "unit": "ratio", "higher_is_better": False,
+                      "builtin": first["builtin_geomean"], "target": 1.05, "by_size": bands,
                       "seconds": round(time.time() - t0, 1)}))
 
 
@@ -1273,6 +1283,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="matrices: skip the vectors, precision and batched workloads in the same line")
     ap.add_argument("--learned-trees", type=int, default=40, help="learned: unseen random trees to evaluate")
+    ap.add_argument("--learned-large-trees", type=int, default=12,
+                    help="learned: unseen random trees on 2^26..2^30-element calls")
     ap.add_argument("--workload", default="matrices",
                     choices=["matrices", "vectors", "precision-bf16", "precision-f16", "batched", "learned", "stats", "convert", "canonical", "views"],
                     help="matrices is the headline line; the others print their own line")

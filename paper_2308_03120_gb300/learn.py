@@ -237,8 +237,8 @@ def _time(fn, budget_us: float = 400.0) -> float:
     return e0.elapsed_time(e1) * 1e3 / reps
 
 
-def _shape(rng, max_log2: int):
-    n = int(2 ** rng.uniform(10, max_log2))
+def _shape(rng, max_log2: int, min_log2: int = 10):
+    n = int(2 ** rng.uniform(min_log2, max_log2))
     r = int(2 ** (rng.uniform(0, 1) * math.log2(n)))
     if r >= 8:
         r -= r % 8  # full-width vector accesses along columns
@@ -248,9 +248,10 @@ def _shape(rng, max_log2: int):
 
 
 def generate(n_trees: int, seed: int, max_log2: int = 26, kinds_per_tree: int = 2,
-             shapes_per_kind: int = 4, threads: int = 16, log=print):
-    """Timing samples for n_trees random trees; every sample holds the
-    per-candidate times (microseconds), features and the built-in time."""
+             shapes_per_kind: int = 4, threads: int = 16, log=print, min_log2: int = 10):
+    """Timing samples for n_trees random trees with element counts
+    2^U[min_log2, max_log2]; every sample holds the per-candidate times
+    (microseconds), features and the built-in time."""
     import torch
 
     import paper_2308_03120_gb300 as coot
@@ -265,7 +266,7 @@ def generate(n_trees: int, seed: int, max_log2: int = 26, kinds_per_tree: int = 
         kinds = rng.choice(KINDS, size=kinds_per_tree, replace=False)
         for k in kinds:
             for s in range(shapes_per_kind):
-                plans.append((t, sexpr, n_in, int(k), dtype, _shape(rng, max_log2)))
+                plans.append((t, sexpr, n_in, int(k), dtype, _shape(rng, max_log2, min_log2)))
     # compile every (tree, kind, dtype, candidate) in parallel threads
     t0 = time.time()
     jobs = set()

@@ -26,16 +26,17 @@ def device():
 
 
 def test_model_beats_the_builtin_shapes_on_unseen_trees():
-    # shapes up to 2^26 elements, as in training: below about 5 M elements
-    # the built-in shapes already shrink the unroll to fill the GPU, so the
-    # model's gain shows over the whole size range
-    samples = learn.generate(16, seed=777, max_log2=26, log=lambda *a: None)
+    # 24 unseen trees (192 calls, fixed seed) on shapes up to 2^26 elements,
+    # as in training; the bar is the target, a geometric-mean regret of at
+    # most 1.05 against the exhaustive tuner (measured 1.028 to 1.037 on
+    # samples of 16 to 32 such trees; the built-in shapes 1.06 to 1.08)
+    samples = learn.generate(24, seed=777, max_log2=26, log=lambda *a: None)
     learn.load_policy()
     learn.use_builtin()
     r = learn.regret(samples, learn.host_predict)
     print("\nunseen trees:", r)
     assert r["model_geomean"] < r["builtin_geomean"]
-    assert r["model_geomean"] <= 1.12
+    assert r["model_geomean"] <= 1.05
 
 
 def test_policy_takes_the_models_argmin():
