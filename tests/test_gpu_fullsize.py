@@ -1,7 +1,8 @@
 """Parity at the workloads' full sizes, through the same calls and launch
-shapes the benchmark times: sampled outputs the oracle computes one by one,
-and full reductions the oracle computes exactly (math.fsum).  The oracle
-works on column blocks so that host memory stays a few GB."""
+shapes the benchmark times: every stored element, every column and row sum
+and the full reductions of the 8192 x 8192 matrix step, sums taken exactly
+by the oracle (math.fsum), and the 2^28-element precision workload.  The
+oracle works on column blocks so that host memory stays a few GB."""
 import math
 
 import numpy as np
@@ -64,13 +65,22 @@ def test_matrix_workload_8192():
     torch.cuda.synchronize()
     s, n2, lo, hi = res.tolist()
 
-    # full reductions over all 67M elements, evaluated by column blocks
+    # every result over all 67M elements, evaluated by column blocks: the
+    # full reductions, every column sum, every row sum (exact per-block
+    # partials of each row, then their sum) and every element of both
+    # stored trees
     allr = np.arange(N)
+    o1 = out1.view(N, N).T.cpu().numpy()  # (rows, cols)
+    o2m = out2.view(N, N).T.cpu().numpy()
+    gc = col.cpu().numpy().astype(np.float64)
+    gr = row.cpu().numpy().astype(np.float64)
     vals, sq, e2, s_abs = [], [], 0.0, 0.0
     olo, ohi, emax = math.inf, -math.inf, 0.0
-    row_blocks = []
-    for c0 in range(0, N, BLOCK_COLS):
-        blk = _sub(host, allr, np.arange(c0, c0 + BLOCK_COLS))
+    row_part = np.zeros((N // BLOCK_COLS, N))
+    row_abs, row_e2 = np.zeros(N), np.zeros(N)
+    for b, c0 in enumerate(range(0, N, BLOCK_COLS)):
+        cidx = np.arange(c0, c0 + BLOCK_COLS)
+        blk = _sub(host, allr, cidx)
         v, bound, unsafe = O.error_bound(t_expr, blk)
         assert not unsafe.any()
         vals.append(v.ravel())
@@ -80,40 +90,35 @@ def test_matrix_workload_8192():
         emax = max(emax, float(bound.max()))
         r32 = O.round_to_format(v, "f32")
         olo, ohi = min(olo, float(r32.min())), max(ohi, float(r32.max()))
-        row_blocks.append((v, bound))
+        # the stored tree: within 1e-5 |v| + 2 E of the oracle, element by element
+        err = np.abs(o1[:, cidx].astype(np.float64) - v)
+        assert np.all(err <= 1e-5 * np.abs(v) + 2.0 * bound), f"stored tree, columns {c0}.."
+        # the sums take the stored FP32 values: each term's bound grows by
+        # its own rounding to FP32
+        errs = np.hypot(bound, v * 2.0 ** -24)
+        want_c = np.array([O._fsum(v[:, j]) for j in range(BLOCK_COLS)])
+        abs_c = np.sum(np.abs(v), axis=0)
+        tol = 1e-6 * np.abs(want_c) + np.where(np.abs(want_c) < 1e-3 * abs_c, 1e-9 * abs_c, 0.0)
+        tol += 6.0 * np.sqrt(np.sum(errs * errs, axis=0))
+        bad = np.abs(gc[cidx] - want_c) > tol
+        assert not bad.any(), f"column sums {cidx[bad][:4]}"
+        row_part[b] = [O._fsum(v[i, :]) for i in range(N)]
+        row_abs += np.sum(np.abs(v), axis=1)
+        row_e2 += np.sum(errs * errs, axis=1)
+        # the exp/sqrt chain, stored: the oracle's own tolerance
+        got2 = np.ascontiguousarray(o2m[:, cidx].ravel(order="F"))
+        check_elementwise(t_chain, blk, synth.as_mat(got2, "f32", N, BLOCK_COLS))
     # (the tolerance needs only sum |t| and sqrt(sum E^2))
     assert_sum_close(s, O._fsum(vals), np.array([s_abs]), np.array([math.sqrt(e2)]), "accu")
     o2 = math.sqrt(O._fsum(sq))
     assert abs(n2 - o2) <= 1e-6 * o2
     assert abs(lo - olo) <= 2 * emax and abs(hi - ohi) <= 2 * emax
     del vals, sq
-
-    # sampled row sums: the oracle's row sums over every column block
-    rng = np.random.default_rng(1)
-    ri = np.sort(rng.choice(N, 64, replace=False))
-    ci = np.sort(rng.choice(N, 64, replace=False))
-    gr = row.cpu().numpy()[ri].astype(np.float64)
-    for k, i in enumerate(ri):
-        terms = np.concatenate([v[i, :] for v, _ in row_blocks])
-        errs = np.concatenate([np.hypot(b[i, :], v[i, :] * 2.0 ** -24) for v, b in row_blocks])
-        assert_sum_close(gr[k], O._fsum(terms), terms, errs, f"row {i}")
-    del row_blocks
-
-    # sampled column sums
-    cols = _sub(host, allr, ci)
-    want = O.sum_dim(t_expr, cols, 0)
-    vb, bb, _ = O.error_bound(t_expr, cols)
-    gc = col.cpu().numpy()[ci].astype(np.float64)
-    for k in range(len(ci)):
-        assert_sum_close(gc[k], want[k], vb[:, k], np.hypot(bb[:, k], vb[:, k] * 2.0 ** -24), f"column {ci[k]}")
-
-    # sampled elements of both stored results
-    sub = _sub(host, ri, ci)
-    o1 = out1.view(N, N).T.cpu().numpy()  # (rows, cols)
-    o2m = out2.view(N, N).T.cpu().numpy()
-    for tree, stored in ((t_expr, o1), (t_chain, o2m)):
-        got = np.ascontiguousarray(stored[np.ix_(ri, ci)].ravel(order="F"))
-        check_elementwise(tree, sub, synth.as_mat(got, "f32", len(ri), len(ci)))
+    want_r = np.array([O._fsum(row_part[:, i]) for i in range(N)])
+    tol = 1e-6 * np.abs(want_r) + np.where(np.abs(want_r) < 1e-3 * row_abs, 1e-9 * row_abs, 0.0)
+    tol += 6.0 * np.sqrt(row_e2)
+    bad = np.abs(gr - want_r) > tol
+    assert not bad.any(), f"row sums {np.nonzero(bad)[0][:4]}"
 
 
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
