@@ -317,6 +317,15 @@ def generate(n_trees: int, seed: int, max_log2: int = 26, kinds_per_tree: int = 
     return samples
 
 
+def merge_sample_sets(first, second, n_first: int):
+    """The samples of two generate() calls as one set: the second call's
+    tree ids are shifted past the first call's n_first trees, so that
+    split_by_tree keeps every tree whole on one side."""
+    for smp in second:
+        smp["tree"] += n_first
+    return first + second
+
+
 def split_by_tree(samples, held_out_frac: float = 0.2, seed: int = 0):
     trees = sorted({s["tree"] for s in samples})
     rng = np.random.default_rng(seed)
@@ -359,6 +368,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=20230806)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--max-log2", type=int, default=26)
+    ap.add_argument("--large-trees", type=int, default=0,
+                    help="further trees timed on calls of 2^26 to 2^30 elements")
+    ap.add_argument("--large-seed", type=int, default=20231127)
     ap.add_argument("--out", default=None, help="report JSON path")
     ap.add_argument("--model", default=MODEL_PATH)
     ap.add_argument("--data", default=None, help="save the timing samples here (pickle)")
@@ -376,6 +388,9 @@ def main(argv=None):
             samples = pickle.load(f)
     else:
         samples = generate(args.trees, args.seed, max_log2=args.max_log2)
+        if args.large_trees > 0:
+            large = generate(args.large_trees, args.large_seed, min_log2=26, max_log2=30)
+            samples = merge_sample_sets(samples, large, args.trees)
     if args.data:
         with open(args.data, "wb") as f:
             pickle.dump(samples, f)
@@ -386,7 +401,8 @@ def main(argv=None):
     train_rmse = float(np.sqrt(np.mean((model.predict(X) - y) ** 2)))
     Xh, yh = design(held)
     held_rmse = float(np.sqrt(np.mean((model.predict(Xh) - yh) ** 2)))
-    model.save(args.model, meta={"trees": args.trees, "train_rows": int(X.shape[0]), "held_rows": int(Xh.shape[0]),
+    model.save(args.model, meta={"trees": args.trees, "large_trees": args.large_trees,
+                                 "train_rows": int(X.shape[0]), "held_rows": int(Xh.shape[0]),
                                  "seed": args.seed, "train_rmse_log": train_rmse, "held_rmse_log": held_rmse})
     _abi.call("coot_model_load", model.params().ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n_params())
     report = {"trees": args.trees, "samples": len(samples), "train_rows": int(X.shape[0]),

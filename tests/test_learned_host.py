@@ -77,3 +77,18 @@ def test_learned_policy_needs_a_model():
     # the policy switch itself must refuse an unknown policy
     with pytest.raises(_abi.CootError):
         _abi.call("coot_set_policy", 7)
+
+
+def test_merged_sample_sets_keep_trees_whole():
+    """Two timing sets (the second from calls of another size band, its
+    trees numbered from 0 again) merge into distinct trees, and the
+    held-out split never puts calls of one tree on both sides."""
+    from paper_2308_03120_gb300 import learn
+    first = [{"tree": t, "call": c} for t in range(10) for c in range(8)]
+    second = [{"tree": t, "call": c, "large": True} for t in range(4) for c in range(8)]
+    merged = learn.merge_sample_sets(first, second, 10)
+    assert len({s["tree"] for s in merged}) == 14
+    assert {s["tree"] for s in merged if s.get("large")} == set(range(10, 14))
+    train, held = learn.split_by_tree(merged)
+    assert {s["tree"] for s in train}.isdisjoint({s["tree"] for s in held})
+    assert len(train) + len(held) == len(merged)
