@@ -445,6 +445,16 @@ coot_status coot_diag(const coot_mat* m, int64_t k, coot_mat* view);
  * second.  Synchronises with the device. */
 coot_status coot_device_status(int* status);
 
+/* The device address of pinned host memory (allocated with cudaHostAlloc /
+ * cudaMallocHost, or registered with cudaHostRegister), for operands that
+ * the kernels read or write in host memory directly: on GB300 the GPU
+ * reaches the Grace CPU's memory coherently over NVLink-C2C, so a fused
+ * kernel can stream its inputs from host memory and store its outputs
+ * there with no staging copy.  `host` may point anywhere inside such an
+ * allocation.  Pageable or unknown memory -> COOT_ERR_INVALID_ARG (no
+ * pointer is ever guessed); the caller keeps ownership.  Host-only. */
+coot_status coot_host_device_pointer(const void* host, void** device);
+
 /* ------------------------------------------------------------------------
  * Statistics along a dimension (Table 6: max/min/sum(A, dim) and the
  * statistics mean/stddev/var(A, dim)), several in ONE pass over the inputs.

@@ -59,12 +59,15 @@ def _dtype_code(t) -> int:
 @dataclass
 class Mat:
     """A column-major n_rows x n_cols matrix over torch storage: element
-    (i, j) is buf[offset + i + j * ld] (buf flattened)."""
+    (i, j) is buf[offset + i + j * ld] (buf flattened).  `base`, when not 0,
+    is the device address of buf's first element (pinned host storage
+    reached over NVLink-C2C; see mapped())."""
     buf: object
     n_rows: int
     n_cols: int
     ld: int
     offset: int = 0
+    base: int = 0
 
     @staticmethod
     def of(t, n_rows: int | None = None, n_cols: int | None = None, ld: int | None = None) -> "Mat":
@@ -82,13 +85,22 @@ class Mat:
 
     def c(self) -> coot_mat:
         t = self.buf
-        ptr = t.data_ptr() + self.offset * t.element_size()
+        ptr = (self.base or t.data_ptr()) + self.offset * t.element_size()
         return coot_mat(ptr, _dtype_code(t), 0, self.n_rows, self.n_cols, self.ld)
+
+    def mapped(self) -> "Mat":
+        """The same matrix over pinned host storage, addressed through its
+        device mapping (coot_host_device_pointer): kernels then read and
+        write host memory directly, with no copy.  Raises CootError for
+        pageable storage."""
+        dev = ctypes.c_void_p()
+        _abi.call("coot_host_device_pointer", ctypes.c_void_p(self.buf.data_ptr()), ctypes.byref(dev))
+        return Mat(self.buf, self.n_rows, self.n_cols, self.ld, self.offset, dev.value)
 
     # ---- submatrix views (coot_submat / coot_diag; Table 1)
     def _view(self, v: coot_mat) -> "Mat":
         es = self.buf.element_size()
-        return Mat(self.buf, v.n_rows, v.n_cols, v.ld, (v.ptr - self.buf.data_ptr()) // es)
+        return Mat(self.buf, v.n_rows, v.n_cols, v.ld, (v.ptr - (self.base or self.buf.data_ptr())) // es, self.base)
 
     def submat(self, r0: int, c0: int, r1: int, c1: int) -> "Mat":
         """Rows r0..r1 and columns c0..c1 (inclusive), sharing storage."""

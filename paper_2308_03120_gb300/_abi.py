@@ -52,6 +52,7 @@ SIGNATURES = {
     "coot_all_any": (c_int, [_u8p, c_size_t, _matp, c_int, _dp, c_void_p, c_size_t, c_void_p]),
     "coot_set_canonical": (c_int, [c_int]),
     "coot_device_status": (c_int, [POINTER(c_int)]),
+    "coot_host_device_pointer": (c_int, [c_void_p, POINTER(c_void_p)]),
     "coot_submat": (c_int, [_matp, c_int64, c_int64, c_int64, c_int64, _matp]),
     "coot_diag": (c_int, [_matp, c_int64, _matp]),
     "coot_tree_canonical": (c_int, [_u8p, c_size_t, c_void_p, c_size_t, POINTER(c_size_t)]),

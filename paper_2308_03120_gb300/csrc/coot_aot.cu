@@ -290,6 +290,21 @@ extern "C" coot_status coot_device_status(int* status) {
   return COOT_OK;
 }
 
+extern "C" coot_status coot_host_device_pointer(const void* host, void** device) {
+  coot::clear_error();
+  if (host == nullptr || device == nullptr) return coot::fail(COOT_ERR_INVALID_ARG, "pointer is NULL");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, host);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return coot::fail(COOT_ERR_INVALID_ARG, std::string("not CUDA host memory: ") + cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr)
+    return coot::fail(COOT_ERR_INVALID_ARG, "not pinned host memory mapped for the device");
+  *device = a.devicePointer;
+  return COOT_OK;
+}
+
 extern "C" {
 
 /* Number of temporaries coot_unfused_eval needs for a tree (one per operator
