@@ -8,7 +8,11 @@
 // line's first element: d = y - K (exact by Sterbenz' lemma whenever y is
 // within a factor of two of K, which is the case that matters -- a mean
 // large against the spread), D1 = sum d and D2 = sum d^2, each group of
-// values added pairwise and the group total with TwoSum.  Then
+// values added pairwise and the group total with TwoSum.  The column
+// statistics form D1 at the end as S - N K in FP64 from the exact sum S
+// (about 48 bits; its error costs about 2 |mean| |mean - K| 2^-48 / var of
+// the variance, far below the bound below) instead of accumulating it,
+// which saves a pairwise sum and a TwoSum per group.  Then
 //   var = (D2 - D1 * D1 / N) / (N - 1 + norm_type)
 // in FP64, where the cancellation costs a factor 1 + (mean - K)^2 / var
 // (about 2 for a typical K) instead of 1 + mean^2 / var.  The error is at
@@ -22,14 +26,17 @@
 #define COOT_ST_STDDEV (1u << 3)
 #define COOT_ST_MIN (1u << 4)
 #define COOT_ST_MAX (1u << 5)
-#define COOT_ST_S1 ((COOT_HEADS & (COOT_ST_SUM | COOT_ST_MEAN)) != 0)
 #define COOT_ST_D ((COOT_HEADS & (COOT_ST_VAR | COOT_ST_STDDEV)) != 0)
+// column statistics (kind 5) form the shifted sum at the end as S - N K from
+// the exact sum instead of accumulating it
+#define COOT_ST_D1S (COOT_KIND == 5)
+#define COOT_ST_S1 ((COOT_HEADS & (COOT_ST_SUM | COOT_ST_MEAN)) != 0 || (COOT_ST_D1S && COOT_ST_D))
 #define COOT_ST_MN ((COOT_HEADS & COOT_ST_MIN) != 0)
 #define COOT_ST_MX ((COOT_HEADS & COOT_ST_MAX) != 0)
-// components of a line's partial: sum (hi, lo), shifted sum (hi, lo),
-// shifted sum of squares (hi, lo), minimum, maximum -- those the
-// statistics need, in that order
-#define COOT_ST_NC (2 * COOT_ST_S1 + 4 * COOT_ST_D + COOT_ST_MN + COOT_ST_MX)
+// components of a line's partial: sum (hi, lo), shifted sum (hi, lo; not
+// for columns), shifted sum of squares (hi, lo), minimum, maximum -- those
+// the statistics need, in that order
+#define COOT_ST_NC (2 * COOT_ST_S1 + (COOT_ST_D1S ? 2 : 4) * COOT_ST_D + COOT_ST_MN + COOT_ST_MX)
 
 // Launch parameters (every field 8 bytes; mirrored on the host).
 struct coot_stats_params {
@@ -55,7 +62,7 @@ struct coot_sacc {
     if constexpr (COOT_ST_S1) coot_two_sum(s, sc, y);
     if constexpr (COOT_ST_D) {
       const COOT_REAL d = y - K;
-      coot_two_sum(d1, d1c, d);
+      if constexpr (!COOT_ST_D1S) coot_two_sum(d1, d1c, d);
       coot_two_sum(d2, d2c, coot_sq(d));
     }
     if constexpr (COOT_ST_MN) mn = coot_min(mn, y);
@@ -68,7 +75,7 @@ struct coot_sacc {
       COOT_REAL d[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) d[g] = y[g] - K;
-      coot_two_sum(d1, d1c, coot_pairwise<G>(d, 0));
+      if constexpr (!COOT_ST_D1S) coot_two_sum(d1, d1c, coot_pairwise<G>(d, 0));
       coot_two_sum(d2, d2c, coot_pairwise<G>(d, 1));
     }
 #pragma unroll
@@ -81,11 +88,18 @@ struct coot_sacc {
   // the components of this accumulator (sums as normalised pairs)
   __device__ __forceinline__ void comps(COOT_REAL (&c)[COOT_ST_NC]) const {
     int k = 0;
-    if constexpr (COOT_ST_S1) { coot_dw_norm(s, sc, c[k], c[k + 1]); k += 2; }
-    if constexpr (COOT_ST_D) {
+    if constexpr (COOT_ST_S1) {
+      coot_dw_norm(s, sc, c[k], c[k + 1]);
+      k += 2;
+    }
+    if constexpr (COOT_ST_D && !COOT_ST_D1S) {
       coot_dw_norm(d1, d1c, c[k], c[k + 1]);
       coot_dw_norm(d2, d2c, c[k + 2], c[k + 3]);
       k += 4;
+    }
+    if constexpr (COOT_ST_D && COOT_ST_D1S) {
+      coot_dw_norm(d2, d2c, c[k], c[k + 1]);
+      k += 2;
     }
     if constexpr (COOT_ST_MN) c[k++] = mn;
     if constexpr (COOT_ST_MX) c[k++] = mx;
@@ -96,7 +110,11 @@ struct coot_sacc {
 __device__ __forceinline__ void coot_st_identity(COOT_REAL (&c)[COOT_ST_NC]) {
   int k = 0;
   if constexpr (COOT_ST_S1) { c[k] = c[k + 1] = (COOT_REAL)0; k += 2; }
-  if constexpr (COOT_ST_D) { c[k] = c[k + 1] = c[k + 2] = c[k + 3] = (COOT_REAL)0; k += 4; }
+  if constexpr (COOT_ST_D) {
+#pragma unroll
+    for (int q = 0; q < (COOT_ST_D1S ? 2 : 4); ++q) c[k + q] = (COOT_REAL)0;
+    k += COOT_ST_D1S ? 2 : 4;
+  }
   if constexpr (COOT_ST_MN) c[k++] = (COOT_REAL)COOT_INF_F;
   if constexpr (COOT_ST_MX) c[k++] = -(COOT_REAL)COOT_INF_F;
   (void)k;
@@ -108,8 +126,8 @@ __device__ __forceinline__ void coot_st_combine(COOT_REAL (&x)[COOT_ST_NC], cons
   if constexpr (COOT_ST_S1) { coot_dw_add(x[k], x[k + 1], y[k], y[k + 1]); k += 2; }
   if constexpr (COOT_ST_D) {
     coot_dw_add(x[k], x[k + 1], y[k], y[k + 1]);
-    coot_dw_add(x[k + 2], x[k + 3], y[k + 2], y[k + 3]);
-    k += 4;
+    if constexpr (!COOT_ST_D1S) coot_dw_add(x[k + 2], x[k + 3], y[k + 2], y[k + 3]);
+    k += COOT_ST_D1S ? 2 : 4;
   }
   if constexpr (COOT_ST_MN) { x[k] = coot_min(x[k], y[k]); ++k; }
   if constexpr (COOT_ST_MX) { x[k] = coot_max(x[k], y[k]); ++k; }
@@ -150,10 +168,17 @@ __device__ void coot_st_store(const coot_stats_params& sp, coot_i64 i, coot_i64 
     s1 = coot_dw_to_double(s1h, s1l);
     k += 2;
   }
-  if constexpr (COOT_ST_D) {
+  if constexpr (COOT_ST_D && !COOT_ST_D1S) {
     d1 = coot_dw_to_double(c[k], c[k + 1]);
     d2 = coot_dw_to_double(c[k + 2], c[k + 3]);
     k += 4;
+  }
+  if constexpr (COOT_ST_D && COOT_ST_D1S) {
+    // the shifted sum from the exact sum: S - N K in FP64 (S carries about
+    // 48 bits, N K is exact up to 2^29 elements)
+    d1 = s1 - (double)N * (double)K;
+    d2 = coot_dw_to_double(c[k], c[k + 1]);
+    k += 2;
   }
   if constexpr (COOT_ST_MN) mn = c[k++];
   if constexpr (COOT_ST_MX) mx = c[k++];
