@@ -413,3 +413,17 @@ def test_several_tree_source_defines_every_slot():
         assert f"COOT_REAL coot_ft{k}(const COOT_REAL* x) {{ return (COOT_REAL)0; }}" in src
     assert "#define COOT_STORE_0 1" in src and "#define COOT_STORE_1 0" in src
     assert "#define COOT_HEADS_1 0u" in src
+
+
+def test_host_device_pointer_refuses_what_it_cannot_map():
+    """A NULL pointer, and host memory the CUDA runtime does not know as
+    pinned (here: a plain ctypes buffer), are refused with
+    COOT_ERR_INVALID_ARG and a message; no address is returned."""
+    dev = ctypes.c_void_p(0)
+    st, msg = _call("coot_host_device_pointer", None, ctypes.byref(dev))
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and msg and dev.value is None
+    buf = ctypes.create_string_buffer(4096)
+    st, msg = _call("coot_host_device_pointer", ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(dev))
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG" and msg and dev.value is None
+    st, _ = _call("coot_host_device_pointer", ctypes.cast(buf, ctypes.c_void_p), None)
+    assert _abi.STATUS[st] == "COOT_ERR_INVALID_ARG"
