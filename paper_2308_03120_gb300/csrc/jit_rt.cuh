@@ -241,8 +241,22 @@ __device__ __forceinline__ void coot_vload(const typename coot_st<S>::T* p, COOT
   } else {
     u.h = coot_ld2(p);
   }
+  if constexpr (S == 1 && B % 4 == 0 && sizeof(COOT_REAL) == 4) {
+    // BF16 pairs widened with a byte permute (low half) and a mask (high
+    // half), both integer-pipe instructions, which leaves the FMA pipes to
+    // the arithmetic of the 2-byte reductions
+    const coot_u32* w = (const coot_u32*)u.e;
 #pragma unroll
-  for (int v = 0; v < V; ++v) x[v] = coot_to_real<S>(u.e[v]);
+    for (int i = 0; i < V / 2; ++i) {
+      coot_u32 lo;
+      asm("prmt.b32 %0, %1, %2, 0x1044;" : "=r"(lo) : "r"(w[i]), "r"(0u));
+      x[2 * i] = __uint_as_float(lo);
+      x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = coot_to_real<S>(u.e[v]);
+  }
 }
 
 template <int S>
