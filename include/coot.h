@@ -99,7 +99,10 @@ typedef enum coot_dtype {
 /* A column-major matrix in device memory: element (i, j), 0 <= i < n_rows,
  * 0 <= j < n_cols, lives at ((T*)ptr)[i + j * ld] with T the storage type.
  * ld >= max(n_rows, 1).  A vector is an n x 1 (column) or 1 x n (row)
- * matrix (Table 1, Col / Row).  n_rows * n_cols == 0 is an empty object. */
+ * matrix (Table 1, Col / Row).  n_rows * n_cols == 0 is an empty object.
+ * ptr may also be the device address of pinned host memory
+ * (coot_host_device_pointer): the kernels then read or write that memory
+ * directly. */
 typedef struct coot_mat {
   void* ptr;
   int32_t dtype; /* coot_dtype */
